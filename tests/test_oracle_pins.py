@@ -1,0 +1,356 @@
+"""Pins for the CPU oracle: closed forms, brute force on tiny inputs, special
+cases that reduce to a library routine, and the worked examples the paper
+prints.  No GPU needed."""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1708_07859_b300 import inputs as gen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def C(n, k):
+    return math.comb(n, k)
+
+
+def rels_for(shape, src, dst):
+    E = list(zip(src.tolist(), dst.tolist()))
+    spec = {
+        "triangle": [(0, 1), (1, 2), (0, 2)],
+        "clique4": [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)],
+        "cycle4": [(0, 1), (1, 2), (2, 3), (0, 3)],
+        "lollipop": [(0, 1), (1, 2), (0, 2), (2, 3)],
+        "path3": [(0, 1), (1, 2), (2, 3)],
+    }[shape]
+    return [{"attrs": a, "tuples": E} for a in spec], (4 if shape != "triangle" else 3)
+
+
+# ------------------------------------------------------------ graph closed forms
+
+@pytest.mark.parametrize("n", [3, 4, 5, 9, 17, 40])
+def test_complete_graph_closed_forms(orc, n):
+    s, d = gen.complete_graph(n)
+    assert orc.triangle_count(s, d) == C(n, 3)
+    assert orc.clique4_count(s, d) == C(n, 4)
+    # every 4-subset a<b<c<d gives exactly one 4-cycle tuple and one lollipop tuple
+    assert orc.cycle4_count(s, d) == C(n, 4)
+    assert orc.lollipop_count(s, d) == C(n, 4)
+
+
+@pytest.mark.parametrize("p,q", [(1, 5), (3, 4), (10, 12)])
+def test_bipartite_has_no_odd_cycles(orc, p, q):
+    s, d = gen.complete_bipartite(p, q)
+    assert orc.triangle_count(s, d) == 0
+    assert orc.clique4_count(s, d) == 0
+    assert orc.lollipop_count(s, d) == 0
+
+
+@pytest.mark.parametrize("n", [4, 5, 8, 31])
+def test_cycle_and_wheel(orc, n):
+    s, d = gen.cycle_graph(n)
+    assert orc.triangle_count(s, d) == 0
+    assert orc.cycle4_count(s, d) == (1 if n == 4 else 0)
+    ws, wd = gen.wheel_graph(n)
+    assert orc.triangle_count(ws, wd) == n          # n > 3: only hub triangles
+
+
+def test_duplicate_and_reversed_edges_are_one_edge(orc):
+    s, d = gen.complete_graph(7)
+    s2 = np.concatenate([s, d, s])
+    d2 = np.concatenate([d, s, d])
+    assert orc.triangle_count(s2, d2) == C(7, 3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("shape", ["triangle", "clique4", "cycle4", "lollipop"])
+def test_graph_counts_match_brute_force(orc, seed, shape):
+    n = 9 if shape != "triangle" else 14
+    m = min(C(n, 2), 14 + 3 * seed)
+    s, d = gen.gnm_edges(n, m, 1000 + seed)
+    rels, k = rels_for(shape, s, d)
+    bf = orc.brute_force_count(k, rels, n)
+    assert orc.GRAPH_COUNT[shape](s, d) == bf
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_rst_join_with_distinct_relations(orc, seed):
+    n = 12
+    R = gen.gnm_edges(n, 20, 2000 + seed)
+    S = gen.gnm_edges(n, 25, 3000 + seed)
+    T = gen.gnm_edges(n, 22, 4000 + seed)
+    rels = [{"attrs": (0, 1), "tuples": list(zip(*[x.tolist() for x in R]))},
+            {"attrs": (1, 2), "tuples": list(zip(*[x.tolist() for x in S]))},
+            {"attrs": (0, 2), "tuples": list(zip(*[x.tolist() for x in T]))}]
+    assert orc.join_rst_count(R, S, T) == orc.brute_force_count(3, rels, n)
+
+
+# ----------------------------------------------------- Algorithm 1 (generic join)
+
+@pytest.mark.parametrize("shape", ["triangle", "cycle4", "lollipop", "path3"])
+def test_generic_join_every_order_same_result(orc, shape):
+    s, d = gen.gnm_edges(10, 24, 77)
+    rels, k = rels_for(shape, s, d)
+    ref = None
+    for order in itertools.permutations(range(k)):
+        res = orc.generic_join(order, rels)
+        canon = sorted(tuple(t[order.index(a)] for a in range(k)) for t in res)
+        if ref is None:
+            ref = canon
+            assert len(ref) == orc.brute_force_count(k, rels, 10)
+        assert canon == ref
+
+
+def test_join_aggregate_sum_product_matches_dense(orc):
+    # SMM as a join-aggregate: C(i,k) = sum_j A(i,j) B(j,k)
+    rng = np.random.default_rng(5)
+    A = (rng.random((6, 7)) < 0.4) * rng.uniform(-1, 1, (6, 7))
+    B = (rng.random((7, 5)) < 0.4) * rng.uniform(-1, 1, (7, 5))
+    ra = {"attrs": (0, 1), "tuples": [(i, j) for i in range(6) for j in range(7) if A[i, j]],
+          "anno": {(i, j): A[i, j] for i in range(6) for j in range(7) if A[i, j]}}
+    rb = {"attrs": (1, 2), "tuples": [(j, k) for j in range(7) for k in range(5) if B[j, k]],
+          "anno": {(j, k): B[j, k] for j in range(7) for k in range(5) if B[j, k]}}
+    out = orc.join_aggregate((0, 2, 1), [ra, rb], semiring="sum", group=(0, 2))
+    Cd = A @ B
+    for (i, k), v in out.items():
+        assert abs(v - Cd[i, k]) < 1e-12
+    pattern = {(i, k) for i in range(6) for k in range(5)
+               if any(A[i, j] and B[j, k] for j in range(7))}
+    assert set(out) == pattern
+
+
+# ------------------------------------------------------------------------ tries
+
+def test_trie_levels_round_trip(orc):
+    rng = np.random.default_rng(3)
+    cols = [rng.integers(0, 5, 60), rng.integers(0, 4, 60), rng.integers(0, 6, 60)]
+    for order in itertools.permutations(range(3)):
+        lv = orc.trie_levels(cols, order)
+        # expand the CSR levels back into tuples
+        tuples = [(int(v),) for v in lv[0][0]]
+        for vals, offs in lv[1:]:
+            nxt = []
+            for p, t in enumerate(tuples):
+                for q in range(int(offs[p]), int(offs[p + 1])):
+                    nxt.append(t + (int(vals[q]),))
+            tuples = nxt
+        want = sorted(set(zip(*[np.asarray(cols[o]).tolist() for o in order])))
+        assert tuples == want
+        for vals, offs in lv[1:]:
+            assert offs[0] == 0 and offs[-1] == vals.size
+            for p in range(offs.size - 1):
+                seg = vals[int(offs[p]):int(offs[p + 1])]
+                assert seg.size > 0 and np.all(np.diff(seg.astype(np.int64)) > 0)
+
+
+def test_intersect_count_vs_sets(orc):
+    for seed in range(5):
+        a = gen.sorted_set(500 + 50 * seed, 4000, seed)
+        b = gen.sorted_set(300, 4000, 100 + seed)
+        assert orc.intersect_count(a, b) == len(set(a.tolist()) & set(b.tolist()))
+
+
+# -------------------------------------------------------------------- sparse LA
+
+def test_spmv_identity_and_dense(orc):
+    n = 64
+    x = gen.dense_vector(n, 1)
+    y, ay = orc.spmv(np.arange(n), np.arange(n), np.ones(n, np.float32), n, x)
+    assert np.array_equal(y, x.astype(np.float64))
+    r, c, v = gen.uniform_coo(50, 40, 7, 9)
+    x = gen.dense_vector(40, 2)
+    Ad = np.zeros((50, 40))
+    Ad[r, c] = v
+    y, ay = orc.spmv(r, c, v, 50, x)
+    assert np.allclose(y, Ad @ x.astype(np.float64), rtol=0, atol=1e-13)
+    assert np.allclose(ay, np.abs(Ad) @ np.abs(x.astype(np.float64)), rtol=0, atol=1e-13)
+
+
+def test_spgemm_rows_vs_dense_and_identities(orc):
+    A = gen.uniform_coo(40, 30, 5, 11)
+    B = gen.uniform_coo(30, 35, 4, 12)
+    Ad = np.zeros((40, 30)); Ad[A[0], A[1]] = A[2]
+    Bd = np.zeros((30, 35)); Bd[B[0], B[1]] = B[2]
+    Cd = Ad @ Bd
+    sel = np.arange(40)
+    off, cols, vals, absv = orc.spgemm_rows(A, 40, B, 30, 35, sel)
+    for i in range(40):
+        ks = cols[off[i]:off[i + 1]]
+        assert np.all(np.diff(ks.astype(np.int64)) > 0)
+        patt = np.flatnonzero((Ad[i] != 0) @ (Bd != 0))
+        assert np.array_equal(ks, patt)
+        assert np.allclose(vals[off[i]:off[i + 1]], Cd[i, ks], rtol=0, atol=1e-13)
+    # A * I = A exactly, P * A a row permutation exactly
+    I = (np.arange(30), np.arange(30), np.ones(30, np.float32))
+    off, cols, vals, _ = orc.spgemm_rows(A, 40, I, 30, 30, sel)
+    for i in range(40):
+        m = A[0] == i
+        order = np.argsort(A[1][m])
+        assert np.array_equal(cols[off[i]:off[i + 1]], A[1][m][order])
+        assert np.array_equal(vals[off[i]:off[i + 1]], A[2][m][order].astype(np.float64))
+    perm = np.random.default_rng(1).permutation(40)
+    P = (np.arange(40), perm, np.ones(40, np.float32))
+    off2, cols2, vals2, _ = orc.spgemm_rows(P, 40, A, 40, 30, sel)
+    off1, cols1, vals1, _ = orc.spgemm_rows(A, 40, I, 30, 30, sel)
+    for i in range(40):
+        j = perm[i]
+        assert np.array_equal(cols2[off2[i]:off2[i + 1]], cols1[off1[j]:off1[j + 1]])
+        assert np.array_equal(vals2[off2[i]:off2[i + 1]], vals1[off1[j]:off1[j + 1]])
+
+
+def test_dense_matmul_small_integers_exact(orc):
+    rng = np.random.default_rng(2)
+    A = rng.integers(-3, 4, (5, 6)).astype(np.float32)
+    B = rng.integers(-3, 4, (6, 4)).astype(np.float32)
+    Cm, Ca = orc.dense_matmul(A, B)
+    for i in range(5):
+        for k in range(4):
+            assert Cm[i, k] == sum(float(A[i, j]) * float(B[j, k]) for j in range(6))
+            assert Ca[i, k] == sum(abs(float(A[i, j]) * float(B[j, k])) for j in range(6))
+
+
+# ---------------------------------------------------------------------- star join
+
+def small_star(n=3000, seed=7):
+    return gen.star_schema(n, dims=(400, 60, 30, 5), seed=seed)
+
+
+def test_star_all_pass_single_group_equals_direct_sum(orc):
+    data = small_star()
+    data = dict(data)
+    data["d3_grp"] = np.zeros_like(data["d3_grp"])
+    data["d4_region"] = np.zeros_like(data["d4_region"])
+    gs, gc = orc.star_sum(data, (-10**9, 10**9), (-10**9, 10**9))
+    direct = math.fsum((data["price"] * (1.0 - data["disc"].astype(np.float64) / 100.0)).tolist())
+    assert gc[0] == data["price"].size and np.all(gc[1:] == 0)
+    assert abs(gs[0] - direct) <= 1e-12 * abs(direct)
+
+
+def test_star_brute_force_and_group_partition(orc):
+    data = small_star(2000, 8)
+    f1, f2 = (300, 1800), (0, 7)
+    gs, gc = orc.star_sum(data, f1, f2)
+    ref = {}
+    k1, k2, k3, k4 = data["k"]
+    for r in range(data["price"].size):
+        if not (f1[0] <= data["d1_date"][k1[r]] <= f1[1]):
+            continue
+        if not (f2[0] <= data["d2_cat"][k2[r]] <= f2[1]):
+            continue
+        g = int(data["d3_grp"][k3[r]]) * 5 + int(data["d4_region"][k4[r]])
+        ref.setdefault(g, []).append(float(data["price"][r]) * (1.0 - int(data["disc"][r]) / 100.0))
+    for g in range(gs.size):
+        vals = ref.get(g, [])
+        assert gc[g] == len(vals)
+        assert abs(gs[g] - math.fsum(vals)) <= 1e-12 * max(1.0, abs(math.fsum(vals)))
+    tot, _ = orc.star_sum(dict(data, d3_grp=np.zeros_like(data["d3_grp"]),
+                               d4_region=np.zeros_like(data["d4_region"])), f1, f2)
+    assert abs(tot[0] - math.fsum(gs.tolist())) <= 1e-9 * abs(tot[0])
+
+
+def test_filter_keys_plain(orc):
+    col = np.array([5, 1, 9, 3, 7, 3], np.int32)
+    assert orc.filter_keys(col, 3, 7).tolist() == [0, 3, 4, 5]
+
+
+# ------------------------------------------------------------ cost model (Sec 4)
+
+def load_q5():
+    with open(os.path.join(GOLDEN, "q5_cost_example.json")) as f:
+        return json.load(f)
+
+
+def test_q5_icost_example(orc):
+    g = load_q5()
+    vid = {v: i for i, v in enumerate(g["vertices"])}
+    rel_attrs = [tuple(vid[a] for a in attrs) for attrs in g["relations"].values()]
+    order = tuple(vid[v] for v in g["order"])
+    assert orc.icosts(order, rel_attrs) == g["icost_printed"]
+
+
+def test_q5_weights_and_cost(orc):
+    g = load_q5()
+    vid = {v: i for i, v in enumerate(g["vertices"])}
+    names = list(g["relations"])
+    rel_attrs = [tuple(vid[a] for a in g["relations"][r]) for r in names]
+    # feed cardinalities that reproduce the printed scores exactly
+    heavy = 59986042
+    cards = []
+    for r in names:
+        target = g["scores_printed"][r]
+        card = (target - 1) * heavy // 100 + 1
+        assert orc.score(card, heavy) == target
+        cards.append(card)
+    # lineitem is the heaviest relation: the scores are relative to it
+    cards = [heavy if r == "lineitem" else c for r, c in zip(names, cards)]
+    w = orc.weights(rel_attrs, cards, ())
+    want = {vid[k]: v for k, v in g["weights_printed"].items()}
+    assert w == want
+    order = tuple(vid[v] for v in g["order"])
+    assert orc.cost(order, rel_attrs, w) == g["cost_derived"]
+
+
+def test_score_from_printed_census(orc):
+    g = load_q5()["score_derived"]
+    assert orc.score(g["card"], g["heavy"]) == g["score"]
+    assert orc.score(5, 5) == 100 and orc.score(1, 10**9) == 1
+
+
+def test_smm_icosts_and_relaxation(orc):
+    smm = load_q5()["smm"]
+    i, k, j = 0, 2, 1
+    rel_attrs = [(i, k), (k, j)]
+    assert orc.icosts((i, j, k), rel_attrs)[2] == smm["icost_k_order_ijk"]
+    assert orc.icosts((i, k, j), rel_attrs)[1] == smm["icost_k_order_ikj"]
+    cands = orc.candidate_orders([i, j, k], materialized={i, j}, rel_attrs=rel_attrs)
+    assert (i, k, j) in cands and (i, j, k) in cands
+    order, c = orc.best_order([i, j, k], rel_attrs, [100, 100], materialized={i, j})
+    assert order == (i, k, j)
+
+
+def test_icost_rules(orc):
+    assert orc.icost_of_layouts(["bs"]) == 0
+    assert orc.icost_of_layouts([]) == 0
+    assert orc.icost_of_layouts(["uint", "bs", "bs"]) == 11
+    assert orc.icost_of_layouts(["uint", "uint", "bs"]) == 60
+    assert orc.icost_of_layouts(["bs", "bs", "bs"]) == 2
+    # a completely dense relation needs no intersection (Section 4.1.1)
+    assert orc.icosts((0, 1), [(0, 1), (1,)], dense={1}) == [0, 0]
+
+
+# ---------------------------------------------------------------------- MLP
+
+def test_mlp_gradient_finite_differences(orc):
+    rng = np.random.default_rng(0)
+    P = orc.mlp_init(7, hidden=8, seed=1)
+    X = rng.normal(size=(11, 7))
+    y = rng.normal(size=11)
+    loss, g = orc.mlp_loss_grad(P, X, y)
+    h = 1e-5
+    for name in P:
+        flat = P[name].reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 7)):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = orc.mlp_loss_grad(P, X, y)
+            flat[idx] = old - h
+            lm, _ = orc.mlp_loss_grad(P, X, y)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (name, idx, fd, an)
+
+
+def test_adam_first_step_moves_by_lr(orc):
+    P = {"w": np.array([1.0, -2.0, 0.5])}
+    G = {"w": np.array([0.3, -4.0, 0.0])}
+    M = {"w": np.zeros(3)}
+    V = {"w": np.zeros(3)}
+    orc.adam_step(P, G, M, V, t=1, lr=0.01)
+    # bias-corrected first step is lr * g / (|g| + eps): lr * sign(g), 0 for g == 0
+    assert np.allclose(P["w"], [1.0 - 0.01, -2.0 + 0.01, 0.5], rtol=0, atol=1e-9)
+    assert np.allclose(M["w"], [0.03, -0.4, 0.0]) and np.allclose(V["w"], [0.00009, 0.016, 0.0])
