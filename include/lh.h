@@ -1,0 +1,407 @@
+/*
+ * lh.h -- C ABI of the B300 (sm_103a) worst-case-optimal join-aggregate
+ * engine, the hot path of LevelHeaded (arXiv 1708.07859).
+ *
+ * Conventions for every entry point
+ *   - Returns lh_status; no exception or abort crosses the ABI.  On failure
+ *     lh_last_error(ctx) holds a one-line reason.
+ *   - "device" pointers are CUDA global-memory addresses on the context's
+ *     device; "host" pointers are ordinary host memory.  Host structs are
+ *     copied during the call.  Device inputs are caller-owned and must stay
+ *     valid until the work that reads them is complete (lh_sync /
+ *     lh_result_wait).
+ *   - All work is issued asynchronously on the context's CUDA stream.  The
+ *     generic join driver reads frontier sizes back to the host between
+ *     chunks (it synchronises the stream there); every other call only
+ *     enqueues work.  Device-side error words (overflow, bounded-wait
+ *     timeouts) surface at lh_sync / lh_result_wait.
+ *   - Objects returned through out-pointers (tries, results, models,
+ *     batches) own device memory until their *_free call.
+ */
+#ifndef LH_H
+#define LH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LH_MAX_LEVELS 6  /* key attributes of one relation (trie levels) */
+#define LH_MAX_ATTRS 6   /* key attributes of one query (hypergraph vertices) */
+#define LH_MAX_EDGES 8   /* relations of one query (hyperedges) */
+#define LH_MAX_ANNOS 4   /* annotation columns of one relation */
+#define LH_NFEAT 60      /* learned-planner feature vector length */
+
+typedef enum {
+    LH_OK = 0,
+    LH_EINVAL = 1,        /* bad argument */
+    LH_ENOMEM = 2,        /* device allocation failed */
+    LH_ECUDA = 3,         /* CUDA runtime error */
+    LH_ETIMEOUT = 4,      /* a bounded device wait or a host time budget ran out */
+    LH_EUNSUPPORTED = 5,  /* shape outside what this build handles */
+    LH_EOVERFLOW = 6      /* a 32-bit offset or capacity would overflow */
+} lh_status;
+
+/* Commutative semirings of the aggregation (AJAR, Section 2.3). */
+typedef enum {
+    LH_COUNT_U64 = 0,      /* (N, +, x), every tuple annotated 1 */
+    LH_SUM_F32_KAHAN = 1,  /* sum of the product of annotations, fp32 compensated,
+                              fp64 final per-group totals */
+    LH_SUM_F64 = 2,        /* as above, totals reported in fp64 (same kernels) */
+    LH_SUMPROD_F32 = 3     /* sum-product of fp32 annotations (sparse LA) */
+} lh_semiring;
+
+typedef enum { LH_T_F32 = 0, LH_T_F64 = 1, LH_T_I8 = 2, LH_T_I32 = 3, LH_T_U32 = 4 } lh_dtype;
+
+typedef struct lh_ctx lh_ctx;
+typedef struct lh_trie lh_trie;
+typedef struct lh_result lh_result;
+typedef struct lh_model lh_model;
+typedef struct lh_batch lh_batch;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = legacy default stream) on which all work is issued.  Device memory
+ * comes from the stream-ordered allocator (cudaMallocAsync) on that stream. */
+lh_status lh_create(lh_ctx **out, void *cuda_stream);
+lh_status lh_destroy(lh_ctx *ctx);
+lh_status lh_set_stream(lh_ctx *ctx, void *cuda_stream);
+/* Last error message of this context (never NULL). */
+const char *lh_last_error(const lh_ctx *ctx);
+/* Wait for the stream; return the first device-side error word, if any. */
+lh_status lh_sync(lh_ctx *ctx);
+/* Library version string. */
+const char *lh_version(void);
+/* Blocking copies between a device pointer and host memory on the context
+ * stream (for reading result arrays back); bytes may be 0. */
+lh_status lh_copy_d2h(lh_ctx *ctx, void *host, const void *dev, uint64_t bytes);
+lh_status lh_copy_h2d(lh_ctx *ctx, void *dev, const void *host, uint64_t bytes);
+
+/* ------------------------------------------------------ tries (Section 2.2) */
+
+/* A relation as key columns and annotation columns (Section 2.1: keys join,
+ * annotations aggregate).  All column pointers are device pointers of length
+ * nrows.  Keys are dictionary-encoded uint32 (identity encoding). */
+typedef struct {
+    uint64_t nrows;
+    uint32_t nkeys;
+    const uint32_t *keys[LH_MAX_LEVELS];
+    uint32_t nannos;
+    const void *annos[LH_MAX_ANNOS];
+    uint32_t anno_types[LH_MAX_ANNOS]; /* lh_dtype */
+} lh_relation_desc;
+
+/* How annotations of duplicate key tuples merge (every tuple has one
+ * annotation, Section 2.3), and which annotation the trie stores.
+ *   LH_MERGE_SUM: float columns (f32/f64) are summed per distinct tuple.
+ *   LH_MERGE_FIRST: the annotation of the first row of the run is kept
+ *     (dimension attributes reached through the metadata container M).
+ *   LH_MERGE_PRICE_DISCOUNT: annos[0] = price (f64 or f32), annos[1] =
+ *     discount in hundredths (i8); the stored annotation is the expression
+ *     price * (1 - discount/100) (Section 3.1, rule 3) as an fp32 compensated
+ *     pair (two f32 columns: high part, low part), duplicates summed. */
+typedef enum { LH_MERGE_SUM = 0, LH_MERGE_FIRST = 1, LH_MERGE_PRICE_DISCOUNT = 2 } lh_merge;
+
+/* Per-set layout choice (Section 2.2: dense sets as bitsets, sparse sets as
+ * sorted uint32).  A set of cardinality c spanning s = max - min + 1 values
+ * gets a bitset when bs_ratio > 0, c >= bs_min_card and c * bs_ratio >= s.
+ * NULL selects {32, 32}.  Every set keeps its sorted uint32 array (used to
+ * iterate); a bitset set additionally has 32-bit words (base = min rounded
+ * down to 128, word count a multiple of 4) and a per-word rank. */
+typedef struct {
+    uint32_t bs_ratio;
+    uint32_t bs_min_card;
+} lh_layout_policy;
+
+/* Build the trie of `rel` with level l holding key column key_order[l]
+ * (key_order: host array, a permutation of [0, nkeys)).  Radix-sorts the
+ * packed key tuples (total key bits <= 64), removes duplicates merging their
+ * annotations per `merge`, emits CSR levels, decides each set's layout and
+ * gathers annotations into leaf order.  Synchronises once (to size levels).
+ * Errors: LH_EINVAL (bad order, nkeys 0 or > LH_MAX_LEVELS, merge/type
+ * mismatch), LH_EUNSUPPORTED (> 64 packed key bits), LH_EOVERFLOW (a level
+ * larger than 2^32 - 1 entries), LH_ENOMEM. */
+lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel, const uint32_t *key_order,
+                        const lh_layout_policy *layout, lh_merge merge, lh_trie **out);
+
+/* Selection pushed into its own relation (Section 3.2): a one-level trie of
+ * the keys k in [0, n) with lo <= col[k] <= hi (col: device int32, length n).
+ * Its single set gets the bitset layout whenever the policy allows. */
+lh_status lh_filter_trie(lh_ctx *ctx, const int32_t *col, uint64_t n, int32_t lo, int32_t hi,
+                         const lh_layout_policy *layout, lh_trie **out);
+
+lh_status lh_trie_free(lh_ctx *ctx, lh_trie *t);
+
+typedef struct {
+    uint32_t nlevels;
+    uint32_t key_order[LH_MAX_LEVELS];
+    uint64_t nrows_in;                     /* rows before duplicate removal */
+    uint64_t level_n[LH_MAX_LEVELS];       /* entries per level */
+    uint64_t level_sets[LH_MAX_LEVELS];    /* sets per level */
+    uint64_t level_bs_sets[LH_MAX_LEVELS]; /* of which bitset layout */
+    uint64_t bitset_words;
+    uint64_t device_bytes;
+} lh_trie_stats;
+
+lh_status lh_trie_stats_get(lh_ctx *ctx, const lh_trie *t, lh_trie_stats *out);
+
+/* Device view of one level.  Sets of level l are indexed by their parent
+ * entry in level l-1 (level 0 has one set, index 0).  The children of entry
+ * p are vals_{l+1}[child_offs[p] .. child_offs[p+1]).  bs_slot[set] is the
+ * set's bitset slot or 0xFFFFFFFF; bs_meta[4*slot + {0,1,2,3}] = {first
+ * word, base value, word count, cardinality}; rank[w] = set bits before word
+ * w inside its set. */
+typedef struct {
+    uint64_t n;
+    uint64_t nsets;
+    const uint32_t *vals;
+    const uint32_t *child_offs; /* NULL at the leaf level */
+    const uint32_t *bs_slot;    /* NULL when the level has no bitset set */
+    uint64_t n_bs;
+    const uint32_t *bs_meta;
+    const uint32_t *words;
+    const uint32_t *rank;
+} lh_level_view;
+
+lh_status lh_trie_level(lh_ctx *ctx, const lh_trie *t, uint32_t level, lh_level_view *out);
+/* Annotation column `col` in leaf order (device pointer) and its lh_dtype. */
+lh_status lh_trie_anno(lh_ctx *ctx, const lh_trie *t, uint32_t col, const void **ptr,
+                       uint32_t *dtype);
+
+/* ------------------------------------- set intersection (Section 4.1.1, Fig 4a) */
+
+/* One set: layout 0 = sorted distinct uint32 (n elements at data), layout 1 =
+ * bitset (n 32-bit words at data, bit b of word w is value base + 32 w + b;
+ * base a multiple of 128, data 16-byte aligned, n a multiple of 4). */
+typedef struct {
+    uint32_t layout;
+    uint32_t base;
+    uint64_t n;
+    const uint32_t *data;
+} lh_set;
+
+/* counts[p] = |A[p] cap B[p]| for p < npairs.  a, b, counts: device arrays.
+ * uint cap uint uses a merge-path partition of each pair across CTAs when
+ * the sizes are within 32x of each other and a binary-search probe of the
+ * smaller into the larger otherwise; uint cap bs tests bits; bs cap bs ANDs
+ * 128-bit words.  Count-only (Section 2.4: the core operation of an
+ * attribute). */
+lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
+                                   const lh_set *b, uint64_t *counts);
+
+/* ----------------------------------------------- queries (Sections 2.3, 3.1) */
+
+/* A hyperedge: relation `trie_slot` of the tries[] argument whose raw key
+ * column c is query attribute attrs[c].  trie_slot = -1 marks a completely
+ * dense unary relation over attrs[0] (a flat fp32 buffer `flat` of length
+ * flat_n: key k present iff k < flat_n, annotation flat[k]); it needs no
+ * intersection (Section 4.1.1, icost 0).  anno: annotation column of the
+ * trie multiplied into each result tuple (-1 = identity).  card: relation
+ * cardinality for the planner (0 = read it from the trie). */
+typedef struct {
+    int32_t trie_slot;
+    uint32_t nattrs;
+    uint32_t attrs[LH_MAX_LEVELS];
+    int32_t anno;
+    const float *flat;
+    uint64_t flat_n;
+    uint64_t card;
+} lh_edge;
+
+/* A GROUP BY column: the int32 annotation column `anno` of edge `edge`'s trie
+ * read at the edge's leaf position (a dimension attribute, Section 5 GROUP BY
+ * annotation), or, with anno = -1, the value of key attribute `attr`.
+ * Values must lie in [0, card). */
+typedef struct {
+    uint32_t edge;
+    int32_t anno;
+    uint32_t attr;
+    uint32_t card;
+} lh_group;
+
+typedef enum {
+    LH_EXEC_AUTO = 0,
+    LH_EXEC_GENERIC = 1, /* attribute-at-a-time frontier expansion (Algorithm 1) */
+    LH_EXEC_SPMV = 2,    /* A(i,j) x(j) group by i, x completely dense */
+    LH_EXEC_SPGEMM = 3   /* A(i,j) B(j,k) group by (i,k), j projected away */
+} lh_exec;
+
+typedef struct {
+    uint32_t n_attrs;
+    uint32_t n_edges;
+    lh_edge edges[LH_MAX_EDGES];
+    uint32_t semiring;          /* lh_semiring */
+    uint32_t n_group;           /* 0..2 */
+    lh_group group[2];
+    uint32_t materialized_mask; /* bit a: attribute a is an output (materialized) */
+    uint32_t eq_selected_mask;  /* bit a: an equality selection touches attribute a */
+    uint32_t exec;              /* lh_exec hint */
+} lh_query;
+
+/* --------------------------------------------------- planner (Section 4) */
+
+typedef enum { LH_PLANNER_COST = 0, LH_PLANNER_LEARNED = 1, LH_PLANNER_EXHAUSTIVE = 2 } lh_planner_kind;
+
+typedef struct {
+    uint32_t n_attrs;
+    uint32_t order[LH_MAX_ATTRS]; /* attribute order: order[0] is processed first */
+    uint32_t bs_ratio;            /* layout policy of the tries this plan runs on (0 = uint only) */
+    uint32_t exec;                /* lh_exec actually used */
+    int64_t cost;                 /* Section 4 cost estimate of `order` */
+    float predicted_log_ms;       /* learned model output (NaN if not used) */
+    float measured_ms;            /* exhaustive timing of the chosen plan (NaN if not used) */
+    uint32_t n_candidates;        /* plans considered */
+} lh_plan_t;
+
+/* Planner options.  time_budget_ms bounds each exhaustive candidate run
+ * (host-side: chunks stop being issued once it is exceeded; the candidate is
+ * then ranked last).  policies: layout ratios tried (0 = uint only). */
+typedef struct {
+    uint32_t n_policies;
+    uint32_t policies[4];
+    float time_budget_ms;
+    uint32_t repeats;
+} lh_plan_opts;
+
+/* Choose an attribute order (and layout policy) for `q`.
+ *   LH_PLANNER_COST: Section 4 cost model (icost x weight, materialized
+ *     attributes first, Section 4.1.2 relaxation, ties to the
+ *     lexicographically smallest order); needs only edge cardinalities.
+ *   LH_PLANNER_LEARNED: scores every (order, policy) with `model` on
+ *     features of tries built from `rels` (both key orders of each relation).
+ *   LH_PLANNER_EXHAUSTIVE: builds the tries of every candidate from `rels`,
+ *     runs and times each, keeps the fastest.
+ * rels: host array of n_edges relation descriptors (may repeat), needed for
+ * LEARNED and EXHAUSTIVE, else NULL.  opts may be NULL. */
+lh_status lh_plan(lh_ctx *ctx, const lh_query *q, lh_planner_kind kind, const lh_model *model,
+                  const lh_relation_desc *const *rels, const lh_plan_opts *opts, lh_plan_t *out);
+
+/* Key order (host array, edge's nattrs entries) of the trie edge `e` must be
+ * built with under `plan`: its key columns sorted by position in plan->order. */
+lh_status lh_edge_key_order(const lh_query *q, const lh_plan_t *plan, uint32_t e,
+                            uint32_t *key_order);
+
+/* -------------------------------------- join-aggregate (Algorithm 1, Sec 5) */
+
+/* Result of one join-aggregate.  Device pointers stay valid until
+ * lh_result_free.  GENERIC: count / sum totals and, with GROUP BY, the dense
+ * per-group arrays (group g = g0 * card1 + g1).  SPMV: y (fp32, nrows).
+ * SPGEMM: CSR C over the nrows distinct rows of A (c_row: their ids,
+ * c_off: nrows+1 uint64, c_col uint32 ascending per row, c_val fp32). */
+typedef struct {
+    uint32_t exec;
+    uint64_t count;
+    double sum;
+    uint32_t ngroups;
+    const double *group_sum;
+    const uint64_t *group_count;
+    uint64_t nrows;
+    const float *y;
+    uint64_t nnz;
+    const uint32_t *c_row;      /* SPGEMM: row id of CSR row r (A's distinct rows, ascending) */
+    const uint64_t *c_off;
+    const uint32_t *c_col;
+    const float *c_val;
+    uint64_t elements;          /* intersection input elements examined (probe count) */
+} lh_result_view;
+
+/* Run query q under plan.  tries: host array of device tries, indexed by
+ * edge.trie_slot; each edge's trie must have been built with the key order
+ * lh_edge_key_order gives for this plan (checked: LH_EINVAL otherwise).
+ * COUNT, SUM (compensated fp32, fp64 totals) and GROUP BY on up to two
+ * columns are supported by the generic driver. */
+lh_status lh_join_aggregate(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
+                            lh_trie *const *tries, lh_result **out);
+/* Wait for the result and fill `view` (host struct; device pointers inside). */
+lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *view);
+lh_status lh_result_free(lh_ctx *ctx, lh_result *r);
+
+/* ------------------------------------------------ dense block (Section 3.1) */
+
+/* C = A B for dense fp32 A (m x k, row-major) and B (k x n, row-major), the
+ * flat annotation buffers attribute elimination leaves (Section 3.1).  A and
+ * B are split into bf16 high parts and bf16 residuals; the product of the
+ * high parts runs on tcgen05 tensor cores with fp32 accumulators in tensor
+ * memory and is written to c_bf16 (fp32, m x n); one refinement step adds
+ * the two residual cross products (fp32 accumulation) and writes the sum in
+ * fp64 to c_refined (m x n; may be NULL to skip the refinement).  m, n, k
+ * must be multiples of 128, 256 and 64 respectively (LH_EUNSUPPORTED
+ * otherwise).  Scratch: 4 bf16 copies of the inputs, from the stream's pool. */
+lh_status lh_dense_matmul(lh_ctx *ctx, const float *A, const float *B, int m, int n, int k,
+                          float *c_bf16, double *c_refined);
+
+/* --------------------------------- batched uneven joins (no paper counterpart) */
+
+typedef enum { LH_BATCH_TRIANGLE = 0, LH_BATCH_CLIQUE4 = 1 } lh_batch_kind;
+
+/* One query of a batch: COUNT of the triangle (or 4-clique) join over the
+ * oriented edge relation E held in `graph`, a 2-level trie built with key
+ * order {0, 1} from edges (src < dst). */
+typedef struct {
+    uint32_t kind;
+    const lh_trie *graph;
+} lh_batch_query;
+
+/* Work-splitting thresholds of the persistent kernel: an outer vertex with
+ * at most t_warp out-edges is handled by one warp with the whole edge range;
+ * larger ones are split into chunks of `chunk` edges; ctas_per_sm sets the
+ * persistent grid (148 SMs x ctas_per_sm CTAs of 256 threads). */
+typedef struct {
+    uint32_t t_warp;
+    uint32_t chunk;
+    uint32_t ctas_per_sm;
+    uint32_t reserved;
+} lh_batch_tuning;
+
+/* Pack n queries into one work list and capture one persistent launch (plus
+ * the reset of its counters) in a CUDA graph.  counts: device uint64[n],
+ * written by every lh_batch_run.  tuning NULL = defaults. */
+lh_status lh_batch_create(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs,
+                          const lh_batch_tuning *tuning, uint64_t *counts, lh_batch **out);
+/* Replay the captured graph on the context stream. */
+lh_status lh_batch_run(lh_ctx *ctx, lh_batch *b);
+lh_status lh_batch_free(lh_ctx *ctx, lh_batch *b);
+/* Sweep tunings on the batch (successive halving over a grid) and return the
+ * fastest; best_ms: its replay time. */
+lh_status lh_batch_autotune(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs, uint64_t *counts,
+                            lh_batch_tuning *best, float *best_ms);
+
+/* ------------------------------------ learned cost model (no paper counterpart) */
+
+/* MLP n_in -> hidden -> hidden -> 1 with ReLU, fp32, parameters in one flat
+ * device buffer: W1 (n_in x hidden, row-major), b1, W2 (hidden x hidden), b2,
+ * W3 (hidden), b3.  Trained with mean squared error and Adam by this
+ * library's own kernels. */
+lh_status lh_model_create(lh_ctx *ctx, uint32_t n_in, uint32_t hidden, uint64_t seed,
+                          lh_model **out);
+lh_status lh_model_free(lh_ctx *ctx, lh_model *m);
+/* Device pointers of the flat parameter and gradient buffers and their length. */
+lh_status lh_model_buffers(lh_ctx *ctx, lh_model *m, float **params, float **grads,
+                           uint64_t *n_params);
+/* out[i] = model(X[i]) for X: device fp32 (n x n_in, row-major). */
+lh_status lh_model_forward(lh_ctx *ctx, const lh_model *m, const float *X, uint32_t n, float *out);
+/* Loss (device fp32 scalar) and gradients (into the model's grad buffer) of
+ * mean((model(X) - y)^2). */
+lh_status lh_model_loss_grad(lh_ctx *ctx, lh_model *m, const float *X, const float *y, uint32_t n,
+                             float *loss);
+/* One Adam step on the model's current gradients (bias-corrected). */
+lh_status lh_model_adam_step(lh_ctx *ctx, lh_model *m, float lr, float beta1, float beta2,
+                             float eps);
+/* Minibatch training: epochs x ceil(n / batch) Adam steps over a seeded
+ * shuffle; final_loss: host, full-set loss after training. */
+lh_status lh_model_train(lh_ctx *ctx, lh_model *m, const float *X, const float *y, uint32_t n,
+                         uint32_t epochs, uint32_t batch, float lr, uint64_t seed,
+                         float *final_loss);
+/* Planner features (host float[LH_NFEAT]) of running q under plan on
+ * `tries` (built for that plan).  Computed on the device from the tries'
+ * level statistics. */
+lh_status lh_plan_features(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
+                           lh_trie *const *tries, float *feat);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LH_H */

@@ -1,0 +1,327 @@
+// Context, error reporting, device scans and the LSD radix sort used by the
+// trie builder (Section 2.2: tries are built from sorted key tuples).
+#include "lh_internal.cuh"
+
+lh_status lh_fail(lh_ctx *ctx, lh_status s, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return s;
+}
+
+extern "C" const char *lh_version(void) { return "lh-b300 0.1 (sm_103a)"; }
+
+extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
+    if (!out) return LH_EINVAL;
+    *out = nullptr;
+    lh_ctx *ctx = new lh_ctx();
+    ctx->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_status, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaHostAlloc((void **)&ctx->h_pinned, lh_ctx::kPinnedWords * sizeof(uint64_t),
+                          cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        delete ctx;
+        return LH_ECUDA;
+    }
+    *out = ctx;
+    return LH_OK;
+}
+
+extern "C" lh_status lh_destroy(lh_ctx *ctx) {
+    if (!ctx) return LH_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+    return LH_OK;
+}
+
+extern "C" lh_status lh_set_stream(lh_ctx *ctx, void *stream) {
+    if (!ctx) return LH_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return LH_OK;
+}
+
+extern "C" const char *lh_last_error(const lh_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" lh_status lh_sync(lh_ctx *ctx) {
+    if (!ctx) return LH_EINVAL;
+    LH_CU(cudaStreamSynchronize(ctx->stream));
+    uint32_t st = 0;
+    LH_CU(cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        LH_CU(cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
+        return lh_fail(ctx, (lh_status)st, "device-side error %u", st);
+    }
+    return LH_OK;
+}
+
+extern "C" lh_status lh_copy_d2h(lh_ctx *ctx, void *host, const void *dev, uint64_t bytes) {
+    if (!ctx || (bytes && (!host || !dev))) return lh_fail(ctx, LH_EINVAL, "null argument");
+    if (!bytes) return LH_OK;
+    LH_CU(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    LH_CU(cudaStreamSynchronize(ctx->stream));
+    return LH_OK;
+}
+
+extern "C" lh_status lh_copy_h2d(lh_ctx *ctx, void *dev, const void *host, uint64_t bytes) {
+    if (!ctx || (bytes && (!host || !dev))) return lh_fail(ctx, LH_EINVAL, "null argument");
+    if (!bytes) return LH_OK;
+    LH_CU(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    LH_CU(cudaStreamSynchronize(ctx->stream));
+    return LH_OK;
+}
+
+lh_status lh_readback(lh_ctx *ctx, const void *dev, size_t bytes, void *host) {
+    if (bytes > lh_ctx::kPinnedWords * sizeof(uint64_t))
+        return lh_fail(ctx, LH_EINVAL, "readback too large");
+    LH_CU(cudaMemcpyAsync(ctx->h_pinned, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    LH_CU(cudaStreamSynchronize(ctx->stream));
+    memcpy(host, ctx->h_pinned, bytes);
+    return LH_OK;
+}
+
+// ---------------------------------------------------------------------- scan
+// Three-phase exclusive scan: per-tile sums, a scan of the tile sums
+// (recursive), then a rescan of every tile seeded with its prefix.
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class TO>
+__device__ TO block_exclusive_scan(TO v, TO *warp_tot, TO &block_total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TO incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        TO t = __shfl_up_sync(LH_FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        TO w = lane < (kScanThreads / 32) ? warp_tot[lane] : TO(0);
+        TO wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            TO t = __shfl_up_sync(LH_FULL, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < (kScanThreads / 32)) warp_tot[lane] = wi - w;
+        if (lane == (kScanThreads / 32) - 1) warp_tot[kScanThreads / 32] = wi;
+    }
+    __syncthreads();
+    TO r = warp_tot[warp] + incl - v;
+    block_total = warp_tot[kScanThreads / 32];
+    __syncthreads();
+    return r;
+}
+
+template <class TI, class TO>
+__global__ void k_tile_sums(const TI *in, uint64_t n, TO *sums) {
+    __shared__ TO wt[kScanThreads / 32 + 1];
+    uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    TO s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += (TO)in[base + k];
+    TO tot;
+    block_exclusive_scan<TO>(s, wt, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <class TI, class TO>
+__global__ void k_tile_scan(const TI *in, uint64_t n, const TO *prefix, TO *out) {
+    __shared__ TO wt[kScanThreads / 32 + 1];
+    uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    TO v[kScanItems];
+    TO s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? (TO)in[base + k] : TO(0);
+        s += v[k];
+    }
+    TO tot;
+    TO run = block_exclusive_scan<TO>(s, wt, tot) + (prefix ? prefix[blockIdx.x] : TO(0));
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    // the thread holding the last element also writes the grand total
+    if (base < n && base + kScanItems >= n) out[n] = run;
+}
+
+template <class TI, class TO>
+lh_status scan_impl(lh_ctx *ctx, const TI *in, TO *out, uint64_t n) {
+    if (n == 0) {
+        LH_CU(cudaMemsetAsync(out, 0, sizeof(TO), ctx->stream));
+        return LH_OK;
+    }
+    uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_tile_scan<TI, TO><<<1, kScanThreads, 0, ctx->stream>>>(in, n, (const TO *)nullptr, out);
+        LH_LAUNCH_CHECK();
+        return LH_OK;
+    }
+    TO *sums = nullptr, *pref = nullptr;
+    LH_TRY(lh_alloc(ctx, &sums, tiles));
+    LH_TRY(lh_alloc(ctx, &pref, tiles + 1));
+    k_tile_sums<TI, TO><<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, sums);
+    LH_LAUNCH_CHECK();
+    lh_status s = scan_impl<TO, TO>(ctx, sums, pref, tiles);
+    if (s == LH_OK) {
+        k_tile_scan<TI, TO><<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, pref, out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "scan: %s", cudaGetErrorString(e));
+    }
+    lh_free(ctx, sums);
+    lh_free(ctx, pref);
+    return s;
+}
+
+}  // namespace
+
+lh_status lh_scan_u32_to_u64(lh_ctx *ctx, const uint32_t *in, uint64_t *out, uint64_t n) {
+    return scan_impl<uint32_t, uint64_t>(ctx, in, out, n);
+}
+lh_status lh_scan_u32_to_u32(lh_ctx *ctx, const uint32_t *in, uint32_t *out, uint64_t n) {
+    return scan_impl<uint32_t, uint32_t>(ctx, in, out, n);
+}
+lh_status lh_scan_u64_to_u64(lh_ctx *ctx, const uint64_t *in, uint64_t *out, uint64_t n) {
+    return scan_impl<uint64_t, uint64_t>(ctx, in, out, n);
+}
+
+// ---------------------------------------------------------------- radix sort
+// LSD, 8-bit digits.  Per pass: per-tile digit histograms (digit-major, so
+// one exclusive scan gives every (digit, tile) its output base), then a
+// stable scatter.  Within a tile, keys are ranked in rounds of 256: lanes
+// with equal digits are grouped by __match_any_sync, warps are ordered by a
+// per-digit prefix over warps, rounds by a running per-digit count.
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per tile
+
+__global__ void k_sort_hist(const uint64_t *keys, uint64_t n, int shift, uint32_t *hist,
+                            uint32_t ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+        uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t n, int shift,
+                               const uint64_t *offs, uint32_t ntiles, uint64_t *kout,
+                               uint32_t *vout) {
+    __shared__ uint32_t wcnt[kSortThreads / 32][256];
+    __shared__ uint32_t running[256];
+    __shared__ uint32_t round_tot[256];
+    __shared__ uint64_t gbase[256];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    gbase[t] = offs[(uint64_t)t * ntiles + blockIdx.x];
+    running[t] = 0;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
+        __syncthreads();
+        uint64_t i = base + (uint64_t)r * kSortThreads + t;
+        bool valid = i < n;
+        uint64_t k = valid ? kin[i] : 0;
+        uint32_t v = valid ? vin[i] : 0;
+        uint32_t d = valid ? (uint32_t)((k >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(LH_FULL, d);
+        uint32_t rk = __popc(peers & lt_mask);
+        if (valid && rk == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t p = 0;
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                uint32_t c = wcnt[w][t];
+                wcnt[w][t] = p;
+                p += c;
+            }
+            round_tot[t] = p;
+        }
+        __syncthreads();
+        if (valid) {
+            uint64_t dst = gbase[d] + running[d] + wcnt[warp][d] + rk;
+            kout[dst] = k;
+            vout[dst] = v;
+        }
+        __syncthreads();
+        running[t] += round_tot[t];
+    }
+}
+
+}  // namespace
+
+lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_t *tmp_k,
+                            uint32_t *tmp_v, uint64_t n, int bits) {
+    if (n <= 1 || bits <= 0) return LH_OK;
+    uint64_t ntiles64 = (n + kSortTile - 1) / kSortTile;
+    if (ntiles64 > (1u << 24)) return lh_fail(ctx, LH_EUNSUPPORTED, "sort: too many keys");
+    uint32_t ntiles = (uint32_t)ntiles64;
+    uint32_t *hist = nullptr;
+    uint64_t *offs = nullptr;
+    LH_TRY(lh_alloc(ctx, &hist, (size_t)256 * ntiles));
+    lh_status s = lh_alloc(ctx, &offs, (size_t)256 * ntiles + 1);
+    if (s != LH_OK) {
+        lh_free(ctx, hist);
+        return s;
+    }
+    uint64_t *ka = keys, *kb = tmp_k;
+    uint32_t *va = vals, *vb = tmp_v;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes && s == LH_OK; ++p) {
+        int shift = 8 * p;
+        k_sort_hist<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, n, shift, hist, ntiles);
+        s = lh_scan_u32_to_u64(ctx, hist, offs, (uint64_t)256 * ntiles);
+        if (s != LH_OK) break;
+        k_sort_scatter<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, va, n, shift, offs, ntiles,
+                                                                  kb, vb);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort: %s", cudaGetErrorString(e));
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    if (s == LH_OK && ka != keys) {
+        cudaError_t e = cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                                        ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                ctx->stream);
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort copy: %s", cudaGetErrorString(e));
+    }
+    lh_free(ctx, hist);
+    lh_free(ctx, offs);
+    return s;
+}

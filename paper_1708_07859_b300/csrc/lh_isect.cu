@@ -1,0 +1,239 @@
+// Count-only set intersection of many independent pairs (the core operation
+// of an attribute, Section 2.4; the three layout pairs of Section 4.1.1 /
+// Figure 4a).  All pairs are cut into fixed-size tiles and one launch
+// drains every tile of every pair:
+//   uint cap uint, sizes within 32x: merge path.  Tile t covers diagonals
+//     [t*TILE, (t+1)*TILE) of the pair's merge; the A and B slices it
+//     consumes are staged in shared memory and every thread merges 16
+//     diagonals.  A match is counted when its A element is consumed and the
+//     current B head equals it, so each is counted exactly once.
+//   uint cap uint, sizes beyond 32x: every element of the smaller set is
+//     binary-searched in the larger.
+//   uint cap bs: every uint element tests one bit.
+//   bs cap bs: 128-bit word AND + popc over the overlapping word range.
+#include "lh_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // merge diagonals (or elements, or words) per tile
+
+enum { K_MERGE = 0, K_PROBE = 1, K_UBS = 2, K_BB = 3, K_EMPTY = 4 };
+
+struct PairPlan {
+    uint32_t kind;
+    uint32_t swap;  // 1: roles of a and b exchanged
+    uint64_t lo_w, hi_w;  // bs cap bs: absolute word range of the overlap
+};
+
+__device__ __forceinline__ uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+__global__ void k_plan(uint32_t npairs, const lh_set *A, const lh_set *B, PairPlan *plan,
+                       uint64_t *tiles) {
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    lh_set a = A[p], b = B[p];
+    PairPlan pl = {K_EMPTY, 0, 0, 0};
+    uint64_t nt = 0;
+    if (a.n > 0 && b.n > 0) {
+        if (a.layout == 0 && b.layout == 0) {
+            uint64_t mn = min(a.n, b.n), mx = max(a.n, b.n);
+            if (mx <= 32 * mn) {
+                pl.kind = K_MERGE;
+                nt = ceil_div(a.n + b.n, kTile);
+            } else {
+                pl.kind = K_PROBE;
+                pl.swap = a.n > b.n;
+                nt = ceil_div(mn, kTile);
+            }
+        } else if (a.layout == 1 && b.layout == 1) {
+            uint64_t a0 = a.base >> 5, b0 = b.base >> 5;
+            uint64_t lo = max(a0, b0), hi = min(a0 + a.n, b0 + b.n);
+            if (hi > lo) {
+                pl.kind = K_BB;
+                pl.lo_w = lo;
+                pl.hi_w = hi;
+                nt = ceil_div(hi - lo, kTile);
+            }
+        } else {
+            pl.kind = K_UBS;
+            pl.swap = a.layout == 1;  // the uint side goes first
+            nt = ceil_div(a.layout == 0 ? a.n : b.n, kTile);
+        }
+    }
+    plan[p] = pl;
+    tiles[p] = nt;
+}
+
+// merge-path split of diagonal d (ties: A first)
+__device__ __forceinline__ uint64_t mp_split(const uint32_t *a, uint64_t na, const uint32_t *b,
+                                             uint64_t nb, uint64_t d) {
+    uint64_t lo = d > nb ? d - nb : 0, hi = min(d, na);
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) <= __ldg(b + d - mid - 1)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t sm_split(const uint32_t *a, uint32_t na, const uint32_t *b,
+                                             uint32_t nb, uint32_t d) {
+    uint32_t lo = d > nb ? d - nb : 0, hi = min(d, na);
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= b[d - mid - 1]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LH_FULL, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(LH_FULL, t, o);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_set *A,
+                                                    const lh_set *B, const PairPlan *plan,
+                                                    const uint64_t *tile_off, uint64_t *counts) {
+    __shared__ uint32_t sa[kTile];
+    __shared__ uint32_t sb[kTile + 1];
+    __shared__ uint64_t bounds[4];
+    __shared__ uint32_t red[kThreads / 32];
+    const uint64_t total = tile_off[npairs];
+    for (uint64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        // pair of this tile
+        uint32_t lo = 0, hi = npairs;
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (tile_off[mid] <= tile) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t p = lo;
+        const uint64_t t = tile - tile_off[p];
+        const PairPlan pl = plan[p];
+        lh_set a = A[p], b = B[p];
+        if (pl.swap) { lh_set x = a; a = b; b = x; }
+        uint32_t cnt = 0;
+        if (pl.kind == K_MERGE) {
+            const uint64_t nd = a.n + b.n;
+            const uint64_t d0 = t * kTile, d1 = min(nd, d0 + kTile);
+            if (threadIdx.x == 0) {
+                uint64_t i0 = mp_split(a.data, a.n, b.data, b.n, d0);
+                bounds[0] = i0;
+                bounds[1] = d0 - i0;
+            } else if (threadIdx.x == 32) {
+                uint64_t i1 = mp_split(a.data, a.n, b.data, b.n, d1);
+                bounds[2] = i1;
+                bounds[3] = d1 - i1;
+            }
+            __syncthreads();
+            const uint64_t i0 = bounds[0], j0 = bounds[1], i1 = bounds[2], j1 = bounds[3];
+            const uint32_t la = (uint32_t)(i1 - i0), lb = (uint32_t)(j1 - j0);
+            const bool has_ext = j1 < b.n;
+            for (uint32_t k = threadIdx.x; k < la; k += kThreads) sa[k] = __ldg(a.data + i0 + k);
+            for (uint32_t k = threadIdx.x; k < lb + (has_ext ? 1u : 0u); k += kThreads)
+                sb[k] = __ldg(b.data + j0 + k);
+            __syncthreads();
+            const uint32_t s = threadIdx.x * kItems;
+            const uint32_t e = min(s + kItems, la + lb);
+            if (s < e) {
+                uint32_t ii = sm_split(sa, la, sb, lb, s);
+                uint32_t jj = s - ii;
+                for (uint32_t step = s; step < e; ++step) {
+                    if (ii < la && (jj >= lb || sa[ii] <= sb[jj])) {
+                        uint32_t av = sa[ii];
+                        bool head = jj < lb || (jj == lb && has_ext);
+                        if (head && sb[jj] == av) ++cnt;
+                        ++ii;
+                    } else {
+                        ++jj;
+                    }
+                }
+            }
+        } else if (pl.kind == K_PROBE) {
+            const uint64_t base = t * kTile;
+            for (uint32_t k = threadIdx.x; k < kTile; k += kThreads) {
+                uint64_t i = base + k;
+                if (i >= a.n) break;
+                uint32_t x = __ldg(a.data + i);
+                uint64_t l = 0, h = b.n;
+                while (l < h) {
+                    uint64_t m = (l + h) >> 1;
+                    if (__ldg(b.data + m) < x) l = m + 1;
+                    else h = m;
+                }
+                cnt += (l < b.n && __ldg(b.data + l) == x) ? 1u : 0u;
+            }
+        } else if (pl.kind == K_UBS) {
+            const uint64_t base = t * kTile;
+            for (uint32_t k = threadIdx.x; k < kTile; k += kThreads) {
+                uint64_t i = base + k;
+                if (i >= a.n) break;
+                uint32_t x = __ldg(a.data + i);
+                if (x >= b.base) {
+                    uint32_t d = x - b.base;
+                    uint64_t w = d >> 5;
+                    if (w < b.n) cnt += (__ldg(b.data + w) >> (d & 31u)) & 1u;
+                }
+            }
+        } else if (pl.kind == K_BB) {
+            // word ranges start on 128-bit boundaries (bases are multiples of
+            // 128 values = 4 words), so uint4 loads are aligned
+            const uint64_t w0 = pl.lo_w + t * kTile, w1 = min(pl.hi_w, w0 + kTile);
+            const uint4 *pa = (const uint4 *)(a.data + (w0 - (a.base >> 5)));
+            const uint4 *pb = (const uint4 *)(b.data + (w0 - (b.base >> 5)));
+            const uint32_t nv = (uint32_t)((w1 - w0) >> 2);
+            for (uint32_t k = threadIdx.x; k < nv; k += kThreads) {
+                uint4 x = __ldg(pa + k), y = __ldg(pb + k);
+                cnt += __popc(x.x & y.x) + __popc(x.y & y.y) + __popc(x.z & y.z) + __popc(x.w & y.w);
+            }
+        }
+        uint32_t tot = block_sum(cnt, red);
+        if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + p), (unsigned long long)tot);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
+                                              const lh_set *b, uint64_t *counts) {
+    if (!ctx) return LH_EINVAL;
+    if (npairs == 0) return LH_OK;
+    if (!a || !b || !counts) return lh_fail(ctx, LH_EINVAL, "null argument");
+    PairPlan *plan = nullptr;
+    uint64_t *tiles = nullptr, *off = nullptr;
+    lh_status s = lh_alloc(ctx, &plan, npairs);
+    if (s == LH_OK) s = lh_alloc(ctx, &tiles, npairs);
+    if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)npairs + 1);
+    if (s == LH_OK) {
+        cudaMemsetAsync(counts, 0, npairs * sizeof(uint64_t), ctx->stream);
+        k_plan<<<lh_blocks(npairs, 256), 256, 0, ctx->stream>>>(npairs, a, b, plan, tiles);
+        s = lh_scan_u64_to_u64(ctx, tiles, off, npairs);
+    }
+    if (s == LH_OK) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect, kThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+        unsigned grid = (unsigned)(ctx->num_sms * per_sm);
+        k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, counts);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "intersect: %s", cudaGetErrorString(e));
+    }
+    lh_free(ctx, plan);
+    lh_free(ctx, tiles);
+    lh_free(ctx, off);
+    return s;
+}

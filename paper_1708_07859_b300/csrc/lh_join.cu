@@ -1,0 +1,639 @@
+// Generic worst-case-optimal join-aggregate driver (Algorithm 1, Section 2.4)
+// with AJAR aggregation (Section 2.3) and GROUP BY on annotations or keys
+// (Section 5).
+//
+// Algorithm 1 recurses one attribute at a time; on the GPU the recursion is
+// unrolled breadth-first in bounded chunks.  The frontier at depth d holds,
+// for every bound prefix tuple, each relation's position in its trie.  For
+// depth d (attribute v = order[d]):
+//   1. sizes:  per frontier entry, the candidate set of every relation that
+//      contains v (its level-0 set, or the children of its bound parent); the
+//      smallest one drives.
+//   2. scan:   exclusive prefix of driver sizes = a flat candidate space, so
+//      that one thread handles one candidate whatever the skew of set sizes.
+//   3. expand: each candidate x of the driver is probed in every other set
+//      (bitset: one word and a rank; uint: binary search) -- the k-way
+//      intersection; survivors become the next frontier (warp-aggregated
+//      compaction), or at the last attribute are counted / aggregated.
+// The candidate space is cut into chunks of at most `cap` candidates, so the
+// frontier memory is bounded whatever the output size; each chunk recurses
+// before the next is expanded (depth-first over chunks).
+#include <chrono>
+#include <cmath>
+
+#include "lh_join.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr uint32_t kSmemGroupsMax = 1024;
+
+enum { M_EMIT = 0, M_COUNT = 1, M_AGG = 2 };
+
+struct JEdge {
+    DTrie t;
+    const float *flat;
+    uint32_t flat_n;
+    uint32_t is_flat;
+    uint32_t anno_kind;  // 0 none, 1 f32, 2 compensated pair
+    const float *a_hi;
+    const float *a_lo;
+};
+
+struct JDepth {
+    uint32_t np;
+    uint8_t e[LH_MAX_EDGES];
+    uint8_t lvl[LH_MAX_EDGES];
+};
+
+struct JQuery {
+    JEdge E[LH_MAX_EDGES];
+    uint32_t ne;
+    JDepth D[LH_MAX_ATTRS];
+    uint32_t nd;
+    uint32_t ngc;                 // group columns
+    uint32_t g_is_key[2];         // 1: key attribute value, 0: int32 annotation column
+    uint32_t g_edge[2];
+    const int32_t *g_col[2];
+    uint32_t g_depth[2];          // depth that binds the key attribute
+    uint32_t g_slot[2];           // frontier slot of a key group value
+    uint32_t g_card[2];
+    uint32_t ngroups;             // 1 when no GROUP BY
+    uint32_t count_only;          // COUNT semiring: no annotation product
+};
+
+__device__ __forceinline__ uint32_t find_entry(const uint64_t *off, uint32_t nF, uint64_t c) {
+    uint32_t lo = 0, hi = nF;  // off[lo] <= c < off[hi]
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_sizes(JQuery q, uint32_t d, const uint32_t *posF, uint32_t nF, uint32_t capF,
+                        uint32_t *size, uint8_t *drv, unsigned long long *elems) {
+    const JDepth &D = q.D[d];
+    uint64_t local = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+        uint32_t best = 0xFFFFFFFFu, bi = 0xFF;
+        uint32_t flat_n = 0xFFFFFFFFu, flat_p = 0xFF;
+        for (uint32_t p = 0; p < D.np; ++p) {
+            const JEdge &E = q.E[D.e[p]];
+            if (E.is_flat) {
+                if (E.flat_n < flat_n) { flat_n = E.flat_n; flat_p = p; }
+                continue;
+            }
+            uint32_t L = D.lvl[p];
+            uint32_t parent = L ? posF[(uint64_t)D.e[p] * capF + i] : 0u;
+            uint32_t lo, hi;
+            lh_set_range(E.t, L, parent, lo, hi);
+            uint32_t sz = hi - lo;
+            local += sz;
+            if (sz < best) { best = sz; bi = p; }
+        }
+        if (bi == 0xFF) { best = flat_n; bi = flat_p; }
+        size[i] = best;
+        drv[i] = (uint8_t)bi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(LH_FULL, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(elems, (unsigned long long)local);
+}
+
+struct ExpandOut {
+    uint32_t *posO;
+    uint32_t capO;
+    uint32_t *gvO;
+    uint32_t *counter;           // survivors emitted
+    unsigned long long *count;   // COUNT without groups
+    double *gsum;
+    unsigned long long *gcount;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const uint32_t *posF,
+                                                     const uint32_t *gvF, uint32_t nF, uint32_t capF,
+                                                     const uint64_t *off, const uint8_t *drv,
+                                                     uint64_t c0, uint64_t c1, ExpandOut o) {
+    extern __shared__ float smem[];
+    const JDepth &D = q.D[d];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const bool use_smem = MODE == M_AGG && q.ngroups <= kSmemGroupsMax;
+    float2 *tab = (float2 *)smem;                                    // [nwarps][ngroups]
+    uint32_t *tcnt = (uint32_t *)(tab + (size_t)nwarps * q.ngroups);  // [nwarps][ngroups]
+    float *stage_h = (float *)(tcnt + (size_t)nwarps * q.ngroups);    // [nwarps][32]
+    float *stage_l = stage_h + nwarps * 32;
+    if (use_smem) {
+        for (uint32_t k = threadIdx.x; k < nwarps * q.ngroups; k += blockDim.x) {
+            tab[k] = make_float2(0.f, 0.f);
+            tcnt[k] = 0;
+        }
+        __syncthreads();
+    }
+    uint32_t my_count = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = c0 + (uint64_t)blockIdx.x * blockDim.x; base < c1; base += stride) {
+        const uint64_t c = base + threadIdx.x;
+        bool ok = c < c1;
+        uint32_t i = 0, x = 0;
+        uint32_t npos[LH_MAX_EDGES];
+        if (ok) {
+            i = find_entry(off, nF, c);
+            const uint32_t j = (uint32_t)(c - off[i]);
+            const uint32_t p0 = drv[i];
+            const JEdge &E0 = q.E[D.e[p0]];
+            if (E0.is_flat) {
+                x = j;
+                npos[p0] = j;
+            } else {
+                const uint32_t L0 = D.lvl[p0];
+                const uint32_t parent = L0 ? posF[(uint64_t)D.e[p0] * capF + i] : 0u;
+                uint32_t lo, hi;
+                lh_set_range(E0.t, L0, parent, lo, hi);
+                x = __ldg(E0.t.lv[L0].vals + lo + j);
+                npos[p0] = lo + j;
+            }
+            for (uint32_t p = 0; p < D.np && ok; ++p) {
+                if (p == p0) continue;
+                const JEdge &E = q.E[D.e[p]];
+                if (E.is_flat) {
+                    ok = x < E.flat_n;
+                    npos[p] = x;
+                    continue;
+                }
+                const uint32_t L = D.lvl[p];
+                const uint32_t parent = L ? posF[(uint64_t)D.e[p] * capF + i] : 0u;
+                uint32_t lo, hi;
+                lh_set_range(E.t, L, parent, lo, hi);
+                ok = lh_probe(E.t, L, L ? parent : 0u, lo, hi, x, &npos[p]);
+            }
+        }
+        if (MODE == M_EMIT) {
+            const uint32_t ball = __ballot_sync(LH_FULL, ok);
+            uint32_t basep = 0;
+            if (lane == 0 && ball) basep = atomicAdd(o.counter, (uint32_t)__popc(ball));
+            basep = __shfl_sync(LH_FULL, basep, 0);
+            if (ok) {
+                const uint32_t slot = basep + __popc(ball & ((1u << lane) - 1u));
+                for (uint32_t e = 0; e < q.ne; ++e) {
+                    uint32_t v = 0;
+                    bool part = false;
+                    for (uint32_t p = 0; p < D.np; ++p)
+                        if (D.e[p] == e) { v = npos[p]; part = true; }
+                    if (!part) v = (d > 0) ? posF[(uint64_t)e * capF + i] : 0u;
+                    o.posO[(uint64_t)e * o.capO + slot] = v;
+                }
+                for (uint32_t g = 0; g < q.ngc; ++g) {
+                    if (!q.g_is_key[g]) continue;
+                    const uint32_t s = q.g_slot[g];
+                    uint32_t v = (q.g_depth[g] == d) ? x : ((d > 0) ? gvF[(uint64_t)s * capF + i] : 0u);
+                    o.gvO[(uint64_t)s * o.capO + slot] = v;
+                }
+            }
+        } else if (MODE == M_COUNT) {
+            my_count += ok ? 1u : 0u;
+        } else {
+            // leaf positions of every relation, the group and the product term
+            uint32_t g = 0;
+            float th = 1.f, tl = 0.f;
+            if (ok) {
+                uint32_t lp[LH_MAX_EDGES];
+                for (uint32_t e = 0; e < q.ne; ++e) {
+                    lp[e] = (d > 0) ? posF[(uint64_t)e * capF + i] : 0u;
+                    for (uint32_t p = 0; p < D.np; ++p)
+                        if (D.e[p] == e) lp[e] = npos[p];
+                }
+                for (uint32_t k = 0; k < q.ngc; ++k) {
+                    uint32_t gv;
+                    if (q.g_is_key[k])
+                        gv = (q.g_depth[k] == d) ? x : gvF[(uint64_t)q.g_slot[k] * capF + i];
+                    else
+                        gv = (uint32_t)__ldg(q.g_col[k] + lp[q.g_edge[k]]);
+                    if (gv >= q.g_card[k]) gv = q.g_card[k] - 1;  // out-of-domain values clamp
+                    g = g * q.g_card[k] + gv;
+                }
+                if (!q.count_only) {
+                    for (uint32_t e = 0; e < q.ne; ++e) {
+                        const JEdge &E = q.E[e];
+                        if (E.anno_kind == 0) continue;
+                        float ah = E.is_flat ? __ldg(E.flat + lp[e]) : __ldg(E.a_hi + lp[e]);
+                        float al = (E.anno_kind == 2) ? __ldg(E.a_lo + lp[e]) : 0.f;
+                        float ph, pe;
+                        lh_two_prod(th, ah, ph, pe);
+                        tl = pe + fmaf(th, al, tl * ah);
+                        th = ph;
+                    }
+                }
+            }
+            if (use_smem) {
+                const uint32_t key = ok ? g : 0xFFFFFFFFu;
+                const uint32_t peers = __match_any_sync(LH_FULL, key);
+                stage_h[warp * 32 + lane] = th;
+                stage_l[warp * 32 + lane] = tl;
+                __syncwarp();
+                if (ok && (peers & ((1u << lane) - 1u)) == 0) {  // leader of its group
+                    float sh = 0.f, sl = 0.f;
+                    uint32_t m = peers;
+                    while (m) {
+                        const int s = __ffs(m) - 1;
+                        m &= m - 1;
+                        lh_pair_add(sh, sl, stage_h[warp * 32 + s], stage_l[warp * 32 + s]);
+                    }
+                    float2 &cell = tab[(size_t)warp * q.ngroups + g];
+                    float ch = cell.x, cl = cell.y;
+                    lh_pair_add(ch, cl, sh, sl);
+                    cell = make_float2(ch, cl);
+                    tcnt[(size_t)warp * q.ngroups + g] += __popc(peers);
+                }
+                __syncwarp();
+            } else if (ok) {
+                atomicAdd(o.gsum + g, (double)th + (double)tl);
+                atomicAdd(o.gcount + g, 1ull);
+            }
+        }
+    }
+    if (MODE == M_COUNT) {
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) my_count += __shfl_xor_sync(LH_FULL, my_count, s);
+        if (lane == 0 && my_count) atomicAdd(o.count, (unsigned long long)my_count);
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (uint32_t g = threadIdx.x; g < q.ngroups; g += blockDim.x) {
+            float sh = 0.f, sl = 0.f;
+            uint32_t cn = 0;
+            for (uint32_t w = 0; w < nwarps; ++w) {
+                float2 cell = tab[(size_t)w * q.ngroups + g];
+                lh_pair_add(sh, sl, cell.x, cell.y);
+                cn += tcnt[(size_t)w * q.ngroups + g];
+            }
+            if (cn) {
+                atomicAdd(o.gsum + g, (double)sh + (double)sl);
+                atomicAdd(o.gcount + g, (unsigned long long)cn);
+            }
+        }
+    }
+}
+
+struct Driver {
+    lh_ctx *ctx;
+    JQuery q;
+    lh_result *r;
+    uint32_t cap;
+    uint32_t n_keygroups;
+    uint32_t mode_last;   // M_COUNT or M_AGG
+    bool shortcut_last;   // last depth has one set and nothing to aggregate: add sizes
+    size_t smem_bytes;
+    unsigned grid_expand;
+    std::chrono::steady_clock::time_point t0;
+    double deadline_ms;
+
+    lh_status check_time() {
+        if (deadline_ms <= 0) return LH_OK;
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > deadline_ms) return lh_fail(ctx, LH_ETIMEOUT, "join exceeded its %.1f ms budget", deadline_ms);
+        return LH_OK;
+    }
+
+    lh_status run(uint32_t d, const uint32_t *posF, const uint32_t *gvF, uint32_t nF, uint32_t capF) {
+        if (nF == 0) return LH_OK;
+        LH_TRY(check_time());
+        uint32_t *size = nullptr;
+        uint8_t *drvb = nullptr;
+        uint64_t *off = nullptr;
+        lh_status s = lh_alloc(ctx, &size, nF);
+        if (s == LH_OK) s = lh_alloc(ctx, &drvb, nF);
+        if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)nF + 1);
+        uint64_t total = 0;
+        if (s == LH_OK) {
+            unsigned g = (unsigned)std::min<uint64_t>(lh_blocks(nF, kThreads), (uint64_t)ctx->num_sms * 8);
+            k_sizes<<<g, kThreads, 0, ctx->stream>>>(q, d, posF, nF, capF, size, drvb,
+                                                     (unsigned long long *)r->d_elems);
+            s = lh_scan_u32_to_u64(ctx, size, off, nF);
+        }
+        if (s == LH_OK) s = lh_readback(ctx, off + nF, sizeof(uint64_t), &total);
+        const bool last = d + 1 == q.nd;
+        if (s == LH_OK && last) {
+            if (shortcut_last) {
+                r->host_count += total;
+            } else if (total) {
+                ExpandOut o = {};
+                o.count = (unsigned long long *)r->d_count;
+                o.gsum = r->d_gsum;
+                o.gcount = (unsigned long long *)r->d_gcount;
+                if (mode_last == M_COUNT)
+                    k_expand<M_COUNT><<<grid_expand, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o);
+                else
+                    k_expand<M_AGG><<<grid_expand, kThreads, smem_bytes, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e));
+            }
+        } else if (s == LH_OK) {
+            for (uint64_t c0 = 0; c0 < total && s == LH_OK; c0 += cap) {
+                const uint64_t c1 = std::min<uint64_t>(total, c0 + cap);
+                const uint32_t capO = (uint32_t)(c1 - c0);
+                uint32_t *posO = nullptr, *gvO = nullptr, *counter = nullptr;
+                s = lh_alloc(ctx, &posO, (size_t)q.ne * capO);
+                if (s == LH_OK) s = lh_alloc(ctx, &gvO, (size_t)std::max(1u, n_keygroups) * capO);
+                if (s == LH_OK) s = lh_alloc(ctx, &counter, 1);
+                uint32_t nO = 0;
+                if (s == LH_OK) {
+                    cudaMemsetAsync(counter, 0, sizeof(uint32_t), ctx->stream);
+                    ExpandOut o = {};
+                    o.posO = posO;
+                    o.capO = capO;
+                    o.gvO = gvO;
+                    o.counter = counter;
+                    unsigned g = (unsigned)std::min<uint64_t>(lh_blocks(c1 - c0, kThreads), grid_expand);
+                    k_expand<M_EMIT><<<g, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, c0, c1, o);
+                    cudaError_t e = cudaGetLastError();
+                    if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e));
+                }
+                if (s == LH_OK) s = lh_readback(ctx, counter, sizeof(uint32_t), &nO);
+                if (s == LH_OK) s = run(d + 1, posO, gvO, nO, capO);
+                lh_free(ctx, posO);
+                lh_free(ctx, gvO);
+                lh_free(ctx, counter);
+            }
+        }
+        lh_free(ctx, size);
+        lh_free(ctx, drvb);
+        lh_free(ctx, off);
+        return s;
+    }
+};
+
+}  // namespace
+
+bool lh_key_order_for(const lh_query *q, const uint32_t *order, uint32_t n_attrs, uint32_t e,
+                      uint32_t *key_order) {
+    if (e >= q->n_edges) return false;
+    const lh_edge &E = q->edges[e];
+    uint32_t pos[LH_MAX_ATTRS];
+    for (uint32_t a = 0; a < LH_MAX_ATTRS; ++a) pos[a] = 0xFFFFFFFFu;
+    for (uint32_t k = 0; k < n_attrs; ++k) {
+        if (order[k] >= LH_MAX_ATTRS) return false;
+        pos[order[k]] = k;
+    }
+    uint32_t idx[LH_MAX_LEVELS];
+    for (uint32_t c = 0; c < E.nattrs; ++c) {
+        if (E.attrs[c] >= LH_MAX_ATTRS || pos[E.attrs[c]] == 0xFFFFFFFFu) return false;
+        idx[c] = c;
+    }
+    std::sort(idx, idx + E.nattrs, [&](uint32_t x, uint32_t y) { return pos[E.attrs[x]] < pos[E.attrs[y]]; });
+    for (uint32_t c = 0; c < E.nattrs; ++c) key_order[c] = idx[c];
+    return true;
+}
+
+extern "C" lh_status lh_edge_key_order(const lh_query *q, const lh_plan_t *plan, uint32_t e,
+                                       uint32_t *key_order) {
+    if (!q || !plan || !key_order) return LH_EINVAL;
+    return lh_key_order_for(q, plan->order, plan->n_attrs, e, key_order) ? LH_OK : LH_EINVAL;
+}
+
+lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
+                         lh_trie *const *tries, lh_result *r, double deadline_ms) {
+    Driver dr;
+    dr.ctx = ctx;
+    dr.r = r;
+    dr.t0 = std::chrono::steady_clock::now();
+    dr.deadline_ms = deadline_ms;
+    JQuery &jq = dr.q;
+    memset(&jq, 0, sizeof(jq));
+    jq.ne = q->n_edges;
+    jq.nd = plan->n_attrs;
+    // edges
+    uint32_t edge_level_attr[LH_MAX_EDGES][LH_MAX_LEVELS];
+    for (uint32_t e = 0; e < q->n_edges; ++e) {
+        const lh_edge &E = q->edges[e];
+        JEdge &J = jq.E[e];
+        if (E.trie_slot < 0) {
+            if (E.nattrs != 1 || !E.flat) return lh_fail(ctx, LH_EINVAL, "flat edge %u needs one attribute and a buffer", e);
+            if (E.flat_n >= (1ull << 32)) return lh_fail(ctx, LH_EOVERFLOW, "flat edge too long");
+            J.is_flat = 1;
+            J.flat = E.flat;
+            J.flat_n = (uint32_t)E.flat_n;
+            J.anno_kind = (E.anno >= 0) ? 1 : 0;
+            edge_level_attr[e][0] = E.attrs[0];
+            continue;
+        }
+        const lh_trie *t = tries[E.trie_slot];
+        if (!t) return lh_fail(ctx, LH_EINVAL, "edge %u: null trie", e);
+        if (t->nlevels != E.nattrs) return lh_fail(ctx, LH_EINVAL, "edge %u: trie has %u levels, edge %u attributes", e, t->nlevels, E.nattrs);
+        uint32_t want[LH_MAX_LEVELS];
+        if (!lh_key_order_for(q, plan->order, plan->n_attrs, e, want)) return lh_fail(ctx, LH_EINVAL, "edge %u: attribute missing from plan", e);
+        for (uint32_t l = 0; l < E.nattrs; ++l)
+            if (t->key_order[l] != want[l]) return lh_fail(ctx, LH_EINVAL, "edge %u: trie key order does not follow the plan's attribute order", e);
+        for (uint32_t l = 0; l < E.nattrs; ++l) {
+            edge_level_attr[e][l] = E.attrs[t->key_order[l]];
+            if (t->lv[l].n >= (1ull << 32) - 1) return lh_fail(ctx, LH_EOVERFLOW, "level too large");
+        }
+        J.t = lh_trie_dview(t);
+        if (E.anno >= 0) {
+            if ((uint32_t)E.anno >= t->nannos) return lh_fail(ctx, LH_EINVAL, "edge %u: no annotation column %d", e, E.anno);
+            uint32_t ty = t->anno_type[E.anno];
+            if (ty != LH_T_F32) return lh_fail(ctx, LH_EUNSUPPORTED, "edge %u: multiplied annotations must be f32", e);
+            J.a_hi = (const float *)t->anno[E.anno];
+            J.anno_kind = 1;
+            // a price/discount trie stores the expression as (high, low) f32 columns 0 and 1
+            if (E.anno == 0 && t->nannos == 2 && t->anno_type[1] == LH_T_F32) {
+                J.a_lo = (const float *)t->anno[1];
+                J.anno_kind = 2;
+            }
+        }
+    }
+    // depths
+    for (uint32_t d = 0; d < plan->n_attrs; ++d) {
+        JDepth &D = jq.D[d];
+        const uint32_t v = plan->order[d];
+        for (uint32_t e = 0; e < q->n_edges; ++e) {
+            const uint32_t nl = q->edges[e].nattrs;
+            for (uint32_t l = 0; l < nl; ++l)
+                if (edge_level_attr[e][l] == v) {
+                    D.e[D.np] = (uint8_t)e;
+                    D.lvl[D.np] = (uint8_t)l;
+                    D.np++;
+                }
+        }
+        if (D.np == 0) return lh_fail(ctx, LH_EINVAL, "attribute %u is in no relation", v);
+        // a relation's level must be bound right after its previous level's attribute
+        for (uint32_t p = 0; p < D.np; ++p) {
+            uint32_t e = D.e[p], l = D.lvl[p];
+            if (l > 0) {
+                uint32_t prev = edge_level_attr[e][l - 1];
+                bool earlier = false;
+                for (uint32_t k = 0; k < d; ++k) earlier |= plan->order[k] == prev;
+                if (!earlier) return lh_fail(ctx, LH_EINVAL, "edge %u level order breaks the plan", e);
+            }
+        }
+    }
+    // groups
+    jq.ngc = q->n_group;
+    jq.ngroups = 1;
+    dr.n_keygroups = 0;
+    if (q->n_group > 2) return lh_fail(ctx, LH_EUNSUPPORTED, "at most two GROUP BY columns");
+    for (uint32_t k = 0; k < q->n_group; ++k) {
+        const lh_group &G = q->group[k];
+        if (G.card == 0) return lh_fail(ctx, LH_EINVAL, "group %u: card 0", k);
+        jq.g_card[k] = G.card;
+        if ((uint64_t)jq.ngroups * G.card > (1ull << 26)) return lh_fail(ctx, LH_EUNSUPPORTED, "group domain above 2^26");
+        jq.ngroups *= G.card;
+        if (G.anno < 0) {
+            jq.g_is_key[k] = 1;
+            jq.g_slot[k] = dr.n_keygroups++;
+            bool found = false;
+            for (uint32_t d = 0; d < plan->n_attrs; ++d)
+                if (plan->order[d] == G.attr) { jq.g_depth[k] = d; found = true; }
+            if (!found) return lh_fail(ctx, LH_EINVAL, "group %u: attribute not in plan", k);
+        } else {
+            if (G.edge >= q->n_edges || q->edges[G.edge].trie_slot < 0) return lh_fail(ctx, LH_EINVAL, "group %u: bad edge", k);
+            const lh_trie *t = tries[q->edges[G.edge].trie_slot];
+            if ((uint32_t)G.anno >= t->nannos || (t->anno_type[G.anno] != LH_T_I32 && t->anno_type[G.anno] != LH_T_U32))
+                return lh_fail(ctx, LH_EINVAL, "group %u: needs an int32 annotation column", k);
+            jq.g_edge[k] = G.edge;
+            jq.g_col[k] = (const int32_t *)t->anno[G.anno];
+        }
+    }
+    const bool is_count = q->semiring == LH_COUNT_U64;
+    jq.count_only = is_count ? 1 : 0;
+    const JDepth &DL = jq.D[jq.nd - 1];
+    uint32_t nonflat = 0;
+    for (uint32_t p = 0; p < DL.np; ++p) nonflat += jq.E[DL.e[p]].is_flat ? 0 : 1;
+    dr.mode_last = (is_count && q->n_group == 0) ? M_COUNT : M_AGG;
+    dr.shortcut_last = dr.mode_last == M_COUNT && DL.np == 1 && nonflat == 1;
+    dr.cap = 1u << 22;
+    dr.smem_bytes = 0;
+    int per_sm = 4;
+    if (dr.mode_last == M_AGG && jq.ngroups <= kSmemGroupsMax) {
+        dr.smem_bytes = (size_t)(kThreads / 32) * jq.ngroups * (sizeof(float2) + sizeof(uint32_t)) +
+                        (size_t)(kThreads / 32) * 32 * 2 * sizeof(float);
+        cudaFuncSetAttribute(k_expand<M_AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dr.smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<M_AGG>, kThreads, dr.smem_bytes);
+        if (per_sm < 1) per_sm = 1;
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<M_COUNT>, kThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    dr.grid_expand = (unsigned)(ctx->num_sms * per_sm);
+    // results
+    r->ngroups = (dr.mode_last == M_AGG) ? jq.ngroups : 0;
+    LH_TRY(res_alloc(ctx, r, &r->d_count, 1));
+    LH_TRY(res_alloc(ctx, r, &r->d_elems, 1));
+    LH_CU(cudaMemsetAsync(r->d_count, 0, sizeof(uint64_t), ctx->stream));
+    LH_CU(cudaMemsetAsync(r->d_elems, 0, sizeof(uint64_t), ctx->stream));
+    if (r->ngroups) {
+        LH_TRY(res_alloc(ctx, r, &r->d_gsum, r->ngroups));
+        LH_TRY(res_alloc(ctx, r, &r->d_gcount, r->ngroups));
+        LH_CU(cudaMemsetAsync(r->d_gsum, 0, r->ngroups * sizeof(double), ctx->stream));
+        LH_CU(cudaMemsetAsync(r->d_gcount, 0, r->ngroups * sizeof(uint64_t), ctx->stream));
+    }
+    // depth 0 starts from the single empty prefix
+    return dr.run(0, nullptr, nullptr, 1, 1);
+}
+
+// ------------------------------------------------------------------- C ABI
+
+static bool is_spmv(const lh_query *q, const lh_plan_t *p) {
+    if (q->n_edges != 2 || q->n_group != 1 || q->group[0].anno >= 0 || p->n_attrs != 2) return false;
+    const lh_edge *A = nullptr, *X = nullptr;
+    for (uint32_t e = 0; e < 2; ++e) (q->edges[e].trie_slot < 0 ? X : A) = &q->edges[e];
+    if (!A || !X || A->nattrs != 2 || X->nattrs != 1 || A->anno != 0) return false;
+    const uint32_t i = q->group[0].attr;
+    return p->order[0] == i && p->order[1] == X->attrs[0] && A->attrs[0] == i && A->attrs[1] == X->attrs[0];
+}
+
+static bool is_spgemm(const lh_query *q, const lh_plan_t *p) {
+    if (q->n_edges != 2 || q->n_group != 2 || p->n_attrs != 3) return false;
+    if (q->group[0].anno >= 0 || q->group[1].anno >= 0) return false;
+    const lh_edge &A = q->edges[0], &B = q->edges[1];
+    if (A.trie_slot < 0 || B.trie_slot < 0 || A.nattrs != 2 || B.nattrs != 2 || A.anno != 0 || B.anno != 0) return false;
+    const uint32_t i = A.attrs[0], j = A.attrs[1], k = B.attrs[1];
+    return B.attrs[0] == j && q->group[0].attr == i && q->group[1].attr == k && p->order[0] == i &&
+           p->order[1] == j && p->order[2] == k;
+}
+
+lh_status lh_join_dispatch(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan, lh_trie *const *tries,
+                           lh_result **out, double deadline_ms) {
+    if (!ctx || !q || !plan || !out) return lh_fail(ctx, LH_EINVAL, "null argument");
+    *out = nullptr;
+    if (q->n_edges == 0 || q->n_edges > LH_MAX_EDGES || plan->n_attrs == 0 || plan->n_attrs > LH_MAX_ATTRS ||
+        plan->n_attrs != q->n_attrs)
+        return lh_fail(ctx, LH_EINVAL, "bad query or plan sizes");
+    for (uint32_t e = 0; e < q->n_edges; ++e)
+        if (q->edges[e].nattrs == 0 || q->edges[e].nattrs > LH_MAX_LEVELS) return lh_fail(ctx, LH_EINVAL, "edge %u: bad arity", e);
+    lh_result *r = new lh_result();
+    r->semiring = q->semiring;
+    lh_status s;
+    uint32_t exec = q->exec;
+    if (exec == LH_EXEC_AUTO) exec = is_spmv(q, plan) ? LH_EXEC_SPMV : is_spgemm(q, plan) ? LH_EXEC_SPGEMM : LH_EXEC_GENERIC;
+    r->exec = exec;
+    if (exec == LH_EXEC_SPMV) {
+        if (!is_spmv(q, plan)) s = lh_fail(ctx, LH_EINVAL, "query is not an SpMV join-aggregate under this plan");
+        else {
+            const lh_edge *A = nullptr, *X = nullptr;
+            for (uint32_t e = 0; e < 2; ++e) (q->edges[e].trie_slot < 0 ? X : A) = &q->edges[e];
+            s = lh_run_spmv(ctx, tries[A->trie_slot], X->flat, X->flat_n, q->group[0].card, r);
+        }
+    } else if (exec == LH_EXEC_SPGEMM) {
+        if (!is_spgemm(q, plan)) s = lh_fail(ctx, LH_EINVAL, "query is not an SpGEMM join-aggregate under this plan");
+        else s = lh_run_spgemm(ctx, tries[q->edges[0].trie_slot], tries[q->edges[1].trie_slot], r);
+    } else {
+        s = lh_run_generic(ctx, q, plan, tries, r, deadline_ms);
+    }
+    if (s != LH_OK) {
+        for (void *p : r->allocs) lh_free(ctx, p);
+        delete r;
+        return s;
+    }
+    *out = r;
+    return LH_OK;
+}
+
+extern "C" lh_status lh_join_aggregate(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
+                                       lh_trie *const *tries, lh_result **out) {
+    return lh_join_dispatch(ctx, q, plan, tries, out, 0.0);
+}
+
+extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v) {
+    if (!ctx || !r || !v) return lh_fail(ctx, LH_EINVAL, "null argument");
+    LH_TRY(lh_sync(ctx));
+    memset(v, 0, sizeof(*v));
+    v->exec = r->exec;
+    uint64_t cnt = 0, el = 0;
+    if (r->d_count) LH_CU(cudaMemcpy(&cnt, r->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
+    if (r->d_elems) LH_CU(cudaMemcpy(&el, r->d_elems, sizeof(el), cudaMemcpyDeviceToHost));
+    v->elements = el;
+    v->count = cnt + r->host_count;
+    if (r->ngroups) {
+        std::vector<double> gs(r->ngroups);
+        std::vector<uint64_t> gc(r->ngroups);
+        LH_CU(cudaMemcpy(gs.data(), r->d_gsum, r->ngroups * sizeof(double), cudaMemcpyDeviceToHost));
+        LH_CU(cudaMemcpy(gc.data(), r->d_gcount, r->ngroups * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        double s = 0.0;
+        uint64_t c = 0;
+        for (uint32_t g = 0; g < r->ngroups; ++g) { s += gs[g]; c += gc[g]; }
+        v->sum = s;
+        v->count = c;
+    }
+    v->ngroups = r->ngroups;
+    v->group_sum = r->d_gsum;
+    v->group_count = r->d_gcount;
+    v->nrows = r->nrows;
+    v->y = r->y;
+    v->nnz = r->nnz;
+    v->c_row = r->c_row;
+    v->c_off = r->c_off;
+    v->c_col = r->c_col;
+    v->c_val = r->c_val;
+    return LH_OK;
+}
+
+extern "C" lh_status lh_result_free(lh_ctx *ctx, lh_result *r) {
+    if (!ctx || !r) return LH_EINVAL;
+    for (void *p : r->allocs) lh_free(ctx, p);
+    delete r;
+    return LH_OK;
+}

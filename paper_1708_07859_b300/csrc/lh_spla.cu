@@ -1,0 +1,368 @@
+// Sparse linear algebra as join-aggregates.
+//
+// SpMV  y(i) = sum_j A(i,j) x(j): x is a completely dense relation, so the
+//   j attribute needs no intersection (Section 4.1.1, icost 0); every row of
+//   A's trie is reduced by a 16-lane group with fp32 error-free products and
+//   compensated sums.
+// SpGEMM C(i,k) = sum_j A(i,j) B(j,k) in the order [i, j, k] with j projected
+//   away before the materialised k (Section 4.1.2 relaxation): per row i,
+//   j ranges over A(i) cap pi_j B (a probe of B's first level), and the k
+//   values of every B(j) are unioned with a GROUP BY on the key k (Section 5)
+//   whose accumulator is a hash table (keys + compensated fp32 value pairs)
+//   in shared memory, or in global memory for rows whose bound exceeds it.
+//   Each row's result is sorted (bitonic) so C's rows are sorted sets.
+#include "lh_join.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ SpMV
+
+constexpr int kSpmvThreads = 256;
+constexpr int kSpmvGroup = 16;
+
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv(DTrie A, const float *av, const float *x,
+                                                       uint32_t x_n, uint32_t nrow_entries, float *y) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (kSpmvGroup - 1);
+    const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / kSpmvGroup;
+    const uint32_t ngroups = (gridDim.x * blockDim.x) / kSpmvGroup;
+    const uint32_t *rows = A.lv[0].vals, *offs = A.lv[0].offs, *cols = A.lv[1].vals;
+    for (uint32_t p0 = group - (group % 2); p0 < nrow_entries; p0 += ngroups) {
+        // both half-warps iterate together so the shuffles stay converged
+        const uint32_t p = p0 + (group % 2);
+        const bool valid = p < nrow_entries;
+        float sh = 0.f, sl = 0.f;
+        if (valid) {
+            const uint32_t lo = __ldg(offs + p), hi = __ldg(offs + p + 1);
+            for (uint32_t q = lo + sub; q < hi; q += kSpmvGroup) {
+                const uint32_t j = __ldg(cols + q);
+                if (j >= x_n) continue;  // x holds keys [0, x_n) only
+                float ph, pl;
+                lh_two_prod(__ldg(av + q), __ldg(x + j), ph, pl);
+                lh_pair_add(sh, sl, ph, pl);
+            }
+        }
+#pragma unroll
+        for (int o = kSpmvGroup / 2; o > 0; o >>= 1) {
+            float oh = __shfl_xor_sync(LH_FULL, sh, o), ol = __shfl_xor_sync(LH_FULL, sl, o);
+            lh_pair_add(sh, sl, oh, ol);
+        }
+        if (valid && sub == 0) y[__ldg(rows + p)] = sh + sl;
+    }
+}
+
+// ---------------------------------------------------------------- SpGEMM
+
+constexpr int kGemmWarps = 4;
+constexpr int kGemmThreads = kGemmWarps * 32;
+constexpr uint32_t kTab = 512;      // shared hash slots per warp
+constexpr uint32_t kSortMax = 256;  // entries sortable in shared memory per warp
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t hash_k(uint32_t k) { return k * 2654435761u; }
+
+// Upper bound of |C(i,.)| per row entry p of A: sum of |B(j)| over j in A(i)
+// that B has.
+__global__ void k_spgemm_bound(DTrie A, DTrie B, uint32_t nA0, uint32_t *ub) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nA0; p += gridDim.x * blockDim.x) {
+        const uint32_t lo = __ldg(A.lv[0].offs + p), hi = __ldg(A.lv[0].offs + p + 1);
+        uint64_t u = 0;
+        for (uint32_t q = lo; q < hi; ++q) {
+            uint32_t pj;
+            if (lh_probe(B, 0, 0, 0, B.lv[0].n, __ldg(A.lv[1].vals + q), &pj))
+                u += __ldg(B.lv[0].offs + pj + 1) - __ldg(B.lv[0].offs + pj);
+        }
+        ub[p] = (uint32_t)(u < 0xFFFFFFFFull ? u : 0xFFFFFFFFull);
+    }
+}
+
+// Global hash capacity for rows above the shared bound (0 for the others).
+__global__ void k_spgemm_gcap(const uint32_t *ub, uint32_t n, uint64_t *gcap) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        uint64_t u = ub[p];
+        uint64_t c = 0;
+        if (u > kTab / 2) {
+            c = 64;
+            while (c < 2 * u) c <<= 1;
+        }
+        gcap[p] = c;
+    }
+}
+
+struct WarpSmem {
+    uint32_t key[kTab];
+    float hi[kTab];
+    float lo[kTab];
+    uint32_t skey[kSortMax];
+    float sval[kSortMax];
+    float st_h[32], st_l[32];
+    uint32_t jb[32], jl[32], jp[32];  // B row start, length, inclusive prefix of lengths
+    float ja[32];                      // A(i,j) value
+};
+
+// (key, value) pairs in [0, n) of warp-visible memory sorted ascending by key
+// (bitonic network over the next power of two, padding keys = kEmpty).
+__device__ void warp_bitonic(uint32_t *key, float *val, uint32_t n, uint32_t npow) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t t = n + lane; t < npow; t += 32) key[t] = kEmpty;
+    __syncwarp();
+    for (uint32_t k = 2; k <= npow; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = lane; t < npow; t += 32) {
+                const uint32_t u = t ^ j;
+                if (u > t) {
+                    const bool up = (t & k) == 0;
+                    const uint32_t a = key[t], b = key[u];
+                    if ((a > b) == up) {
+                        key[t] = b;
+                        key[u] = a;
+                        const float va = val[t];
+                        val[t] = val[u];
+                        val[u] = va;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kGemmThreads) k_spgemm_numeric(
+    DTrie A, const float *av, DTrie B, const float *bv, uint32_t nA0, const uint64_t *tmp_off,
+    const uint64_t *goff, uint32_t *gkey, float *ghi, float *glo, uint32_t *tcol, float *tval,
+    uint32_t *cnt) {
+    __shared__ WarpSmem sm_all[kGemmWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem &S = sm_all[warp];
+    const uint32_t gw = blockIdx.x * kGemmWarps + warp;
+    const uint32_t nw = gridDim.x * kGemmWarps;
+    for (uint32_t p = gw; p < nA0; p += nw) {
+        const uint64_t cap64 = goff[p + 1] - goff[p];
+        const bool global = cap64 > 0;
+        const uint32_t cap = global ? (uint32_t)cap64 : kTab;
+        uint32_t *key = global ? gkey + goff[p] : S.key;
+        float *th = global ? ghi + goff[p] : S.hi;
+        float *tl = global ? glo + goff[p] : S.lo;
+        for (uint32_t s = lane; s < cap; s += 32) {
+            key[s] = kEmpty;
+            th[s] = 0.f;
+            tl[s] = 0.f;
+        }
+        __syncwarp();
+        const uint32_t alo = __ldg(A.lv[0].offs + p), ahi = __ldg(A.lv[0].offs + p + 1);
+        for (uint32_t q0 = alo; q0 < ahi; q0 += 32) {
+            // stage up to 32 (j, a) of this row with their B row ranges
+            const uint32_t q = q0 + lane;
+            uint32_t bstart = 0, blen = 0;
+            float a = 0.f;
+            if (q < ahi) {
+                uint32_t pj;
+                if (lh_probe(B, 0, 0, 0, B.lv[0].n, __ldg(A.lv[1].vals + q), &pj)) {
+                    bstart = __ldg(B.lv[0].offs + pj);
+                    blen = __ldg(B.lv[0].offs + pj + 1) - bstart;
+                    a = __ldg(av + q);
+                }
+            }
+            uint32_t incl = blen;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(LH_FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            S.jb[lane] = bstart;
+            S.jl[lane] = blen;
+            S.jp[lane] = incl;
+            S.ja[lane] = a;
+            const uint32_t total = __shfl_sync(LH_FULL, incl, 31);
+            __syncwarp();
+            for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                const bool act = t < total;
+                uint32_t k = kEmpty;
+                float ph = 0.f, pl = 0.f;
+                if (act) {
+                    uint32_t lo = 0, hi = 31;  // first staged j with prefix > t
+                    while (lo < hi) {
+                        uint32_t mid = (lo + hi) >> 1;
+                        if (S.jp[mid] > t) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    const uint32_t pos = S.jb[lo] + (t - (S.jp[lo] - S.jl[lo]));
+                    k = __ldg(B.lv[1].vals + pos);
+                    lh_two_prod(S.ja[lo], __ldg(bv + pos), ph, pl);
+                }
+                // lanes that share a k merge their terms first, then one lane updates
+                const uint32_t peers = __match_any_sync(LH_FULL, k);
+                S.st_h[lane] = ph;
+                S.st_l[lane] = pl;
+                __syncwarp();
+                if (act && (peers & ((1u << lane) - 1u)) == 0) {
+                    float sh = 0.f, sl = 0.f;
+                    uint32_t m = peers;
+                    while (m) {
+                        const int s = __ffs(m) - 1;
+                        m &= m - 1;
+                        lh_pair_add(sh, sl, S.st_h[s], S.st_l[s]);
+                    }
+                    uint32_t slot = hash_k(k) & (cap - 1);
+                    for (uint32_t probe = 0; probe < cap; ++probe) {
+                        const uint32_t prev = atomicCAS(&key[slot], kEmpty, k);
+                        if (prev == kEmpty || prev == k) break;
+                        slot = (slot + 1) & (cap - 1);
+                    }
+                    float ch = th[slot], cl = tl[slot];
+                    lh_pair_add(ch, cl, sh, sl);
+                    th[slot] = ch;
+                    tl[slot] = cl;
+                }
+                __syncwarp();
+            }
+        }
+        // compact occupied slots, sort by k, write the row to its temporary range
+        uint32_t n = 0;
+        uint32_t *ok_ = global ? gkey + goff[p] : S.skey;  // compaction target
+        float *ov = global ? ghi + goff[p] : S.sval;
+        if (!global) {
+            for (uint32_t s0 = 0; s0 < cap; s0 += 32) {
+                const uint32_t s = s0 + lane;
+                const bool occ = s < cap && key[s] != kEmpty;
+                const uint32_t b = __ballot_sync(LH_FULL, occ);
+                if (occ) {
+                    const uint32_t d = n + __popc(b & ((1u << lane) - 1u));
+                    ok_[d] = key[s];
+                    ov[d] = th[s] + tl[s];
+                }
+                n += __popc(b);
+            }
+        } else {
+            // in place: compacted index never passes the slot it reads
+            for (uint32_t s0 = 0; s0 < cap; s0 += 32) {
+                const uint32_t s = s0 + lane;
+                const bool occ = s < cap && key[s] != kEmpty;
+                const uint32_t kk = occ ? key[s] : 0u;
+                const float vv = occ ? th[s] + tl[s] : 0.f;
+                const uint32_t b = __ballot_sync(LH_FULL, occ);
+                __syncwarp();
+                if (occ) {
+                    const uint32_t d = n + __popc(b & ((1u << lane) - 1u));
+                    ok_[d] = kk;
+                    ov[d] = vv;
+                }
+                n += __popc(b);
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        uint32_t npow = 1;
+        while (npow < n) npow <<= 1;
+        if (n > 1) warp_bitonic(ok_, ov, n, npow);
+        const uint64_t t0 = tmp_off[p];
+        for (uint32_t s = lane; s < n; s += 32) {
+            tcol[t0 + s] = ok_[s];
+            tval[t0 + s] = ov[s];
+        }
+        if (lane == 0) cnt[p] = n;
+        __syncwarp();
+    }
+}
+
+__global__ void k_spgemm_gather(uint32_t nA0, const uint64_t *tmp_off, const uint64_t *c_off,
+                                const uint32_t *tcol, const float *tval, uint32_t *ccol, float *cval) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t p = gw; p < nA0; p += nw) {
+        const uint64_t s0 = tmp_off[p], d0 = c_off[p], n = c_off[p + 1] - d0;
+        for (uint64_t s = lane; s < n; s += 32) {
+            ccol[d0 + s] = tcol[s0 + s];
+            cval[d0 + s] = tval[s0 + s];
+        }
+    }
+}
+
+}  // namespace
+
+lh_status lh_run_spmv(lh_ctx *ctx, const lh_trie *a, const float *x, uint64_t x_n, uint64_t nrows,
+                      lh_result *r) {
+    if (a->nlevels != 2 || a->nannos < 1 || a->anno_type[0] != LH_T_F32)
+        return lh_fail(ctx, LH_EINVAL, "SpMV needs a 2-level trie with an f32 annotation");
+    if (x_n >= (1ull << 32) || nrows >= (1ull << 32)) return lh_fail(ctx, LH_EOVERFLOW, "SpMV sizes");
+    r->nrows = nrows;
+    LH_TRY(res_alloc(ctx, r, &r->y, nrows));
+    LH_CU(cudaMemsetAsync(r->y, 0, nrows * sizeof(float), ctx->stream));
+    const uint32_t n0 = (uint32_t)a->lv[0].n;
+    if (n0 == 0) return LH_OK;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv, kSpmvThreads, 0);
+    unsigned grid = std::min<unsigned>(lh_blocks((uint64_t)n0 * kSpmvGroup, kSpmvThreads),
+                                       (unsigned)(ctx->num_sms * std::max(1, per_sm)));
+    k_spmv<<<grid, kSpmvThreads, 0, ctx->stream>>>(lh_trie_dview(a), (const float *)a->anno[0], x,
+                                                   (uint32_t)x_n, n0, r->y);
+    LH_LAUNCH_CHECK();
+    return LH_OK;
+}
+
+lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_result *r) {
+    if (a->nlevels != 2 || b->nlevels != 2 || a->nannos < 1 || b->nannos < 1 ||
+        a->anno_type[0] != LH_T_F32 || b->anno_type[0] != LH_T_F32)
+        return lh_fail(ctx, LH_EINVAL, "SpGEMM needs 2-level tries with f32 annotations");
+    const uint32_t n0 = (uint32_t)a->lv[0].n;
+    const DTrie A = lh_trie_dview(a), B = lh_trie_dview(b);
+    r->nrows = n0;
+    r->c_row = a->lv[0].vals;
+    LH_TRY(res_alloc(ctx, r, &r->c_off, (size_t)n0 + 1));
+    uint32_t *ub = nullptr, *cnt = nullptr, *gkey = nullptr, *tcol = nullptr;
+    uint64_t *tmp_off = nullptr, *gcap = nullptr, *goff = nullptr;
+    float *ghi = nullptr, *glo = nullptr, *tval = nullptr;
+    lh_status s = LH_OK;
+    uint64_t U = 0, G = 0, nnz = 0;
+    const unsigned T = 256;
+    const unsigned grid = (unsigned)std::min<uint64_t>(lh_blocks(n0, T), (uint64_t)ctx->num_sms * 8);
+#define STEP(x) if (s == LH_OK) s = (x)
+    STEP(lh_alloc(ctx, &ub, n0));
+    STEP(lh_alloc(ctx, &cnt, n0));
+    STEP(lh_alloc(ctx, &tmp_off, (size_t)n0 + 1));
+    STEP(lh_alloc(ctx, &gcap, n0));
+    STEP(lh_alloc(ctx, &goff, (size_t)n0 + 1));
+    if (s == LH_OK && n0) {
+        k_spgemm_bound<<<grid, T, 0, ctx->stream>>>(A, B, n0, ub);
+        k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(ub, n0, gcap);
+    }
+    STEP(lh_scan_u32_to_u64(ctx, ub, tmp_off, n0));
+    STEP(lh_scan_u64_to_u64(ctx, gcap, goff, n0));
+    STEP(lh_readback(ctx, tmp_off + n0, sizeof(uint64_t), &U));
+    STEP(lh_readback(ctx, goff + n0, sizeof(uint64_t), &G));
+    STEP(lh_alloc(ctx, &tcol, U));
+    STEP(lh_alloc(ctx, &tval, U));
+    STEP(lh_alloc(ctx, &gkey, G));
+    STEP(lh_alloc(ctx, &ghi, G));
+    STEP(lh_alloc(ctx, &glo, G));
+    if (s == LH_OK && n0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spgemm_numeric, kGemmThreads, 0);
+        unsigned g2 = (unsigned)std::min<uint64_t>((n0 + kGemmWarps - 1) / kGemmWarps,
+                                                   (uint64_t)ctx->num_sms * std::max(1, per_sm));
+        k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
+                                                               (const float *)b->anno[0], n0, tmp_off,
+                                                               goff, gkey, ghi, glo, tcol, tval, cnt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "spgemm: %s", cudaGetErrorString(e));
+    }
+    STEP(lh_scan_u32_to_u64(ctx, cnt, r->c_off, n0));
+    STEP(lh_readback(ctx, r->c_off + n0, sizeof(uint64_t), &nnz));
+    if (s == LH_OK) {
+        r->nnz = nnz;
+        s = res_alloc(ctx, r, &r->c_col, nnz);
+        STEP(res_alloc(ctx, r, &r->c_val, nnz));
+    }
+    if (s == LH_OK && n0)
+        k_spgemm_gather<<<grid, T, 0, ctx->stream>>>(n0, tmp_off, r->c_off, tcol, tval, r->c_col, r->c_val);
+#undef STEP
+    lh_free(ctx, ub); lh_free(ctx, cnt); lh_free(ctx, tmp_off); lh_free(ctx, gcap); lh_free(ctx, goff);
+    lh_free(ctx, tcol); lh_free(ctx, tval); lh_free(ctx, gkey); lh_free(ctx, ghi); lh_free(ctx, glo);
+    if (s == LH_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "spgemm: %s", cudaGetErrorString(e));
+    }
+    return s;
+}

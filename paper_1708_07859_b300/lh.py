@@ -1,0 +1,573 @@
+"""ctypes binding of liblh (include/lh.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers and C structs and back.  Importing it loads
+``liblh.so`` from this package directory and raises if it is missing or if
+no CUDA device is present when a context is created -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblh.so")
+
+MAX_LEVELS = 6
+MAX_ATTRS = 6
+MAX_EDGES = 8
+MAX_ANNOS = 4
+NFEAT = 60
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EOVERFLOW = range(7)
+COUNT_U64, SUM_F32_KAHAN, SUM_F64, SUMPROD_F32 = range(4)
+T_F32, T_F64, T_I8, T_I32, T_U32 = range(5)
+MERGE_SUM, MERGE_FIRST, MERGE_PRICE_DISCOUNT = range(3)
+EXEC_AUTO, EXEC_GENERIC, EXEC_SPMV, EXEC_SPGEMM = range(4)
+PLANNER_COST, PLANNER_LEARNED, PLANNER_EXHAUSTIVE = range(3)
+BATCH_TRIANGLE, BATCH_CLIQUE4 = range(2)
+
+STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ENOMEM", 3: "LH_ECUDA", 4: "LH_ETIMEOUT",
+                5: "LH_EUNSUPPORTED", 6: "LH_EOVERFLOW"}
+
+
+class LHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ----------------------------------------------------------------- structs
+
+class RelationDesc(C.Structure):
+    _fields_ = [("nrows", C.c_uint64), ("nkeys", C.c_uint32),
+                ("keys", C.c_void_p * MAX_LEVELS), ("nannos", C.c_uint32),
+                ("annos", C.c_void_p * MAX_ANNOS), ("anno_types", C.c_uint32 * MAX_ANNOS)]
+
+
+class LayoutPolicy(C.Structure):
+    _fields_ = [("bs_ratio", C.c_uint32), ("bs_min_card", C.c_uint32)]
+
+
+class TrieStats(C.Structure):
+    _fields_ = [("nlevels", C.c_uint32), ("key_order", C.c_uint32 * MAX_LEVELS),
+                ("nrows_in", C.c_uint64), ("level_n", C.c_uint64 * MAX_LEVELS),
+                ("level_sets", C.c_uint64 * MAX_LEVELS), ("level_bs_sets", C.c_uint64 * MAX_LEVELS),
+                ("bitset_words", C.c_uint64), ("device_bytes", C.c_uint64)]
+
+
+class LevelView(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("nsets", C.c_uint64), ("vals", C.c_void_p),
+                ("child_offs", C.c_void_p), ("bs_slot", C.c_void_p), ("n_bs", C.c_uint64),
+                ("bs_meta", C.c_void_p), ("words", C.c_void_p), ("rank", C.c_void_p)]
+
+
+class Set(C.Structure):
+    _fields_ = [("layout", C.c_uint32), ("base", C.c_uint32), ("n", C.c_uint64), ("data", C.c_void_p)]
+
+
+class Edge(C.Structure):
+    _fields_ = [("trie_slot", C.c_int32), ("nattrs", C.c_uint32), ("attrs", C.c_uint32 * MAX_LEVELS),
+                ("anno", C.c_int32), ("flat", C.c_void_p), ("flat_n", C.c_uint64), ("card", C.c_uint64)]
+
+
+class Group(C.Structure):
+    _fields_ = [("edge", C.c_uint32), ("anno", C.c_int32), ("attr", C.c_uint32), ("card", C.c_uint32)]
+
+
+class Query(C.Structure):
+    _fields_ = [("n_attrs", C.c_uint32), ("n_edges", C.c_uint32), ("edges", Edge * MAX_EDGES),
+                ("semiring", C.c_uint32), ("n_group", C.c_uint32), ("group", Group * 2),
+                ("materialized_mask", C.c_uint32), ("eq_selected_mask", C.c_uint32),
+                ("exec", C.c_uint32)]
+
+
+class Plan(C.Structure):
+    _fields_ = [("n_attrs", C.c_uint32), ("order", C.c_uint32 * MAX_ATTRS), ("bs_ratio", C.c_uint32),
+                ("exec", C.c_uint32), ("cost", C.c_int64), ("predicted_log_ms", C.c_float),
+                ("measured_ms", C.c_float), ("n_candidates", C.c_uint32)]
+
+    def order_list(self):
+        return [int(self.order[i]) for i in range(self.n_attrs)]
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("n_policies", C.c_uint32), ("policies", C.c_uint32 * 4),
+                ("time_budget_ms", C.c_float), ("repeats", C.c_uint32)]
+
+
+class ResultView(C.Structure):
+    _fields_ = [("exec", C.c_uint32), ("count", C.c_uint64), ("sum", C.c_double),
+                ("ngroups", C.c_uint32), ("group_sum", C.c_void_p), ("group_count", C.c_void_p),
+                ("nrows", C.c_uint64), ("y", C.c_void_p), ("nnz", C.c_uint64), ("c_row", C.c_void_p),
+                ("c_off", C.c_void_p), ("c_col", C.c_void_p), ("c_val", C.c_void_p),
+                ("elements", C.c_uint64)]
+
+
+class BatchQuery(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("graph", C.c_void_p)]
+
+
+class BatchTuning(C.Structure):
+    _fields_ = [("t_warp", C.c_uint32), ("chunk", C.c_uint32), ("ctas_per_sm", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+# ----------------------------------------------------------------- library
+
+EXPORTS = {
+    "lh_create": [C.c_void_p, C.c_void_p],
+    "lh_destroy": [C.c_void_p],
+    "lh_set_stream": [C.c_void_p, C.c_void_p],
+    "lh_sync": [C.c_void_p],
+    "lh_copy_d2h": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
+    "lh_copy_h2d": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
+    "lh_build_trie": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "lh_filter_trie": [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p],
+    "lh_trie_free": [C.c_void_p, C.c_void_p],
+    "lh_trie_stats_get": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_trie_level": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
+    "lh_trie_anno": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p],
+    "lh_intersect_count_batch": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_plan": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_edge_key_order": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
+    "lh_join_aggregate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_result_wait": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_result_free": [C.c_void_p, C.c_void_p],
+    "lh_dense_matmul": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "lh_batch_create": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_batch_run": [C.c_void_p, C.c_void_p],
+    "lh_batch_free": [C.c_void_p, C.c_void_p],
+    "lh_batch_autotune": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_model_create": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
+    "lh_model_free": [C.c_void_p, C.c_void_p],
+    "lh_model_buffers": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_model_forward": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
+    "lh_model_loss_grad": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
+    "lh_model_adam_step": [C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float],
+    "lh_model_train": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32,
+                       C.c_uint32, C.c_float, C.c_uint64, C.c_void_p],
+    "lh_plan_features": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded liblh.so (raises if the CUDA library was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblh.so not found at {LIB_PATH}: run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, args in EXPORTS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.lh_last_error.argtypes = [C.c_void_p]
+        L.lh_last_error.restype = C.c_char_p
+        L.lh_version.argtypes = []
+        L.lh_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return C.c_void_p(0) if t is None else C.c_void_p(t.data_ptr())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def to_device_u32(a, device="cuda"):
+    """numpy uint32 array -> torch int32 CUDA tensor holding the same bits."""
+    torch = _torch()
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return torch.from_numpy(a.view(np.int32)).to(device)
+
+
+def u32_to_numpy(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+# ----------------------------------------------------------------- objects
+
+class Context:
+    """An lh_ctx bound to the current torch CUDA stream (or ``stream``)."""
+
+    def __init__(self, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblh needs a CUDA device; there is no CPU fallback")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        self.h = C.c_void_p()
+        self._check(lib().lh_create(C.byref(self.h), C.c_void_p(s.cuda_stream)))
+
+    def _check(self, st):
+        if st != OK:
+            msg = lib().lh_last_error(self.h).decode() if self.h else ""
+            raise LHError(st, msg)
+
+    def close(self):
+        if self.h:
+            lib().lh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def sync(self):
+        self._check(lib().lh_sync(self.h))
+
+    def set_stream(self, s):
+        self.stream = s
+        self._check(lib().lh_set_stream(self.h, C.c_void_p(s.cuda_stream)))
+
+    # --- tries -----------------------------------------------------------
+    def build_trie(self, keys, key_order=None, annos=(), merge=MERGE_SUM, layout=None):
+        """keys: list of CUDA int32/uint32 tensors (same length); annos: list
+        of (tensor, lh_dtype).  Returns a Trie."""
+        desc = RelationDesc()
+        desc.nrows = int(keys[0].numel()) if keys else 0
+        desc.nkeys = len(keys)
+        for i, k in enumerate(keys):
+            desc.keys[i] = k.data_ptr()
+        desc.nannos = len(annos)
+        for i, (t, ty) in enumerate(annos):
+            desc.annos[i] = t.data_ptr()
+            desc.anno_types[i] = ty
+        order = (C.c_uint32 * MAX_LEVELS)(*(key_order if key_order is not None else range(len(keys))))
+        pol = None
+        if layout is not None:
+            pol = LayoutPolicy(*layout)
+        out = C.c_void_p()
+        self._check(lib().lh_build_trie(self.h, C.byref(desc), order,
+                                        C.byref(pol) if pol is not None else None, merge, C.byref(out)))
+        return Trie(self, out, keep=(keys, annos))
+
+    def filter_trie(self, col, lo, hi, layout=None):
+        pol = LayoutPolicy(*layout) if layout is not None else None
+        out = C.c_void_p()
+        self._check(lib().lh_filter_trie(self.h, _ptr(col), int(col.numel()), int(lo), int(hi),
+                                         C.byref(pol) if pol is not None else None, C.byref(out)))
+        return Trie(self, out, keep=(col,))
+
+    # --- intersections -----------------------------------------------------
+    def intersect_count_batch(self, a_sets, b_sets, counts):
+        """a_sets, b_sets: CUDA uint8 tensors holding packed lh_set arrays."""
+        n = a_sets.numel() // C.sizeof(Set)
+        self._check(lib().lh_intersect_count_batch(self.h, n, _ptr(a_sets), _ptr(b_sets), _ptr(counts)))
+
+    # --- planning / joins ----------------------------------------------------
+    def plan(self, q, kind=PLANNER_COST, model=None, rels=None, opts=None):
+        p = Plan()
+        rel_arr = None
+        if rels is not None:
+            rel_arr = (C.POINTER(RelationDesc) * len(rels))(*[C.pointer(r) for r in rels])
+        self._check(lib().lh_plan(self.h, C.byref(q), kind, model.h if model is not None else None,
+                                  rel_arr, C.byref(opts) if opts is not None else None, C.byref(p)))
+        return p
+
+    def edge_key_order(self, q, plan, e):
+        ko = (C.c_uint32 * MAX_LEVELS)()
+        self._check(lib().lh_edge_key_order(C.byref(q), C.byref(plan), e, ko))
+        return [int(ko[i]) for i in range(q.edges[e].nattrs)]
+
+    def join_aggregate(self, q, plan, tries):
+        arr = (C.c_void_p * max(1, len(tries)))(*[t.h.value if t is not None else None for t in tries])
+        out = C.c_void_p()
+        self._check(lib().lh_join_aggregate(self.h, C.byref(q), C.byref(plan), arr, C.byref(out)))
+        return Result(self, out)
+
+    def dense_matmul(self, A, B, c_bf16, c_refined=None):
+        m, k = A.shape
+        n = B.shape[1]
+        self._check(lib().lh_dense_matmul(self.h, _ptr(A), _ptr(B), m, n, k, _ptr(c_bf16), _ptr(c_refined)))
+
+
+class Trie:
+    def __init__(self, ctx, h, keep=()):
+        self.ctx, self.h, self._keep = ctx, h, keep
+
+    def free(self):
+        if self.h:
+            lib().lh_trie_free(self.ctx.h, self.h)
+            self.h = C.c_void_p()
+
+    def stats(self):
+        s = TrieStats()
+        self.ctx._check(lib().lh_trie_stats_get(self.ctx.h, self.h, C.byref(s)))
+        return s
+
+    def level(self, l):
+        v = LevelView()
+        self.ctx._check(lib().lh_trie_level(self.ctx.h, self.h, l, C.byref(v)))
+        return v
+
+    def level_arrays(self, l):
+        """Copy one level to host numpy arrays (vals, child_offs or None, bitset info)."""
+        v = self.level(l)
+        out = {"vals": _dev_to_np(v.vals, v.n, np.uint32, self.ctx)}
+        out["offs"] = _dev_to_np(v.child_offs, v.n + 1, np.uint32, self.ctx) if v.child_offs else None
+        out["n_bs"] = int(v.n_bs)
+        if v.bs_slot:
+            out["bs_slot"] = _dev_to_np(v.bs_slot, v.nsets, np.uint32, self.ctx)
+            out["bs_meta"] = _dev_to_np(v.bs_meta, 4 * v.n_bs, np.uint32, self.ctx).reshape(-1, 4)
+        return out
+
+    def anno_array(self, col):
+        p = C.c_void_p()
+        ty = C.c_uint32()
+        self.ctx._check(lib().lh_trie_anno(self.ctx.h, self.h, col, C.byref(p), C.byref(ty)))
+        n = self.stats().level_n[self.stats().nlevels - 1]
+        dt = {T_F32: np.float32, T_F64: np.float64, T_I8: np.int8, T_I32: np.int32, T_U32: np.uint32}[ty.value]
+        return _dev_to_np(p.value, n, dt, self.ctx)
+
+    def words(self):
+        v = self.level(0)
+        nw = self.stats().bitset_words
+        return (_dev_to_np(v.words, nw, np.uint32, self.ctx) if nw else np.zeros(0, np.uint32),
+                _dev_to_np(v.rank, nw, np.uint32, self.ctx) if nw else np.zeros(0, np.uint32))
+
+
+def _dev_to_np(ptr, n, dtype, ctx=None):
+    """Copy n elements from a raw device pointer into a numpy array (through
+    the library's blocking lh_copy_d2h)."""
+    n = int(n)
+    nbytes = n * np.dtype(dtype).itemsize
+    host = np.empty(max(nbytes, 1), dtype=np.uint8)
+    if nbytes:
+        c = ctx or _default_ctx()
+        c._check(lib().lh_copy_d2h(c.h, C.c_void_p(host.ctypes.data), C.c_void_p(ptr), nbytes))
+    return host[:nbytes].view(dtype)
+
+
+_DEFAULT = None
+
+
+def _default_ctx():
+    global _DEFAULT
+    if _DEFAULT is None:
+        _DEFAULT = Context()
+    return _DEFAULT
+
+
+class Result:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+        self.view = None
+
+    def wait(self):
+        v = ResultView()
+        self.ctx._check(lib().lh_result_wait(self.ctx.h, self.h, C.byref(v)))
+        self.view = v
+        return v
+
+    def groups(self):
+        v = self.view or self.wait()
+        return (_dev_to_np(v.group_sum, v.ngroups, np.float64, self.ctx),
+                _dev_to_np(v.group_count, v.ngroups, np.uint64, self.ctx))
+
+    def y(self):
+        v = self.view or self.wait()
+        return _dev_to_np(v.y, v.nrows, np.float32, self.ctx)
+
+    def csr(self):
+        v = self.view or self.wait()
+        return (_dev_to_np(v.c_row, v.nrows, np.uint32, self.ctx), _dev_to_np(v.c_off, v.nrows + 1, np.uint64, self.ctx),
+                _dev_to_np(v.c_col, v.nnz, np.uint32, self.ctx), _dev_to_np(v.c_val, v.nnz, np.float32, self.ctx))
+
+    def free(self):
+        if self.h:
+            lib().lh_result_free(self.ctx.h, self.h)
+            self.h = C.c_void_p()
+
+
+# ----------------------------------------------------------------- queries
+
+def make_query(n_attrs, edges, semiring=COUNT_U64, group=(), materialized=(), eq_selected=(),
+               exec_hint=EXEC_AUTO):
+    """edges: list of dicts {slot, attrs, anno=-1, flat=None (tensor), card=0};
+    group: list of dicts {edge, anno=-1, attr=0, card}."""
+    q = Query()
+    q.n_attrs = n_attrs
+    q.n_edges = len(edges)
+    for i, e in enumerate(edges):
+        E = q.edges[i]
+        E.trie_slot = e.get("slot", -1)
+        attrs = e["attrs"]
+        E.nattrs = len(attrs)
+        for c, a in enumerate(attrs):
+            E.attrs[c] = a
+        E.anno = e.get("anno", -1)
+        flat = e.get("flat")
+        if flat is not None:
+            E.flat = flat.data_ptr()
+            E.flat_n = flat.numel()
+        E.card = e.get("card", 0)
+    q.semiring = semiring
+    q.n_group = len(group)
+    for i, g in enumerate(group):
+        q.group[i].edge = g.get("edge", 0)
+        q.group[i].anno = g.get("anno", -1)
+        q.group[i].attr = g.get("attr", 0)
+        q.group[i].card = g["card"]
+    q.materialized_mask = sum(1 << a for a in materialized)
+    q.eq_selected_mask = sum(1 << a for a in eq_selected)
+    q.exec = exec_hint
+    return q
+
+
+def make_plan(order, bs_ratio=32, exec_kind=EXEC_AUTO):
+    p = Plan()
+    p.n_attrs = len(order)
+    for i, a in enumerate(order):
+        p.order[i] = a
+    p.bs_ratio = bs_ratio
+    p.exec = exec_kind
+    p.cost = -1
+    p.predicted_log_ms = math.nan
+    p.measured_ms = math.nan
+    return p
+
+
+def pack_sets(sets):
+    """List of (layout, base, n, data_ptr) -> bytes of an lh_set array."""
+    arr = (Set * len(sets))(*[Set(l, b, n, p) for (l, b, n, p) in sets])
+    return bytes(arr)
+
+
+# ----------------------------------------------------------- graph helpers
+
+GRAPH_SHAPES = {
+    "triangle": (3, [(0, 1), (1, 2), (0, 2)]),
+    "clique4": (4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]),
+    "cycle4": (4, [(0, 1), (1, 2), (2, 3), (0, 3)]),
+    "lollipop": (4, [(0, 1), (1, 2), (0, 2), (2, 3)]),
+    "path3": (4, [(0, 1), (1, 2), (2, 3)]),
+    "star3": (4, [(0, 1), (0, 2), (0, 3)]),
+}
+
+
+class GraphJoin:
+    """COUNT of a graph pattern join over one oriented edge relation E(src,
+    dst): each pattern edge is a hyperedge on E.  Tries of E are built in the
+    key orders the plan needs (forward (src, dst) and reverse (dst, src))."""
+
+    def __init__(self, ctx, src_dev, dst_dev, shape, layout=(32, 32)):
+        self.ctx = ctx
+        self.src, self.dst = src_dev, dst_dev
+        self.n_attrs, self.pattern = GRAPH_SHAPES[shape]
+        self.layout = layout
+        self.tries = {}
+        card = int(src_dev.numel())
+        self.query = make_query(self.n_attrs, [{"slot": 0, "attrs": list(p), "card": card}
+                                               for p in self.pattern])
+
+    def trie(self, key_order, layout=None):
+        lay = tuple(layout or self.layout)
+        k = (tuple(key_order), lay)
+        if k not in self.tries:
+            self.tries[k] = self.ctx.build_trie([self.src, self.dst], key_order=list(key_order), layout=lay)
+        return self.tries[k]
+
+    def run(self, plan, layout=None):
+        """Returns (count, elements, result view) under ``plan``."""
+        tries = []
+        q = Query()
+        C.memmove(C.byref(q), C.byref(self.query), C.sizeof(Query))
+        slots = {}
+        for e in range(q.n_edges):
+            ko = self.ctx.edge_key_order(self.query, plan, e)
+            key = tuple(ko)
+            if key not in slots:
+                slots[key] = len(tries)
+                tries.append(self.trie(ko, layout))
+            q.edges[e].trie_slot = slots[key]
+        r = self.ctx.join_aggregate(q, plan, tries)
+        v = r.wait()
+        out = (int(v.count), int(v.elements))
+        r.free()
+        return out
+
+    def free(self):
+        for t in self.tries.values():
+            t.free()
+        self.tries.clear()
+
+
+# ------------------------------------------------------- star-schema helper
+
+class StarJoin:
+    """Star-schema join-aggregate over Fact(k1..k4) with the annotation
+    price * (1 - discount) (Section 3.1 rule 3), selections pushed into filter
+    relations on D1 and D2 (Section 3.2), GROUP BY two dimension attributes
+    reached through D3 and D4 (Section 5).  Attributes: k1=0, k2=1, k3=2,
+    k4=3."""
+
+    def __init__(self, ctx, keys, price, disc, d3_grp, d4_region, n_g1=100, n_g2=5,
+                 key_order=(0, 1, 2, 3), layout=None):
+        import torch
+        self.ctx = ctx
+        self.n_g1, self.n_g2 = n_g1, n_g2
+        self.fact = ctx.build_trie(list(keys), key_order=list(key_order),
+                                   annos=[(price, T_F64 if price.dtype == torch.float64 else T_F32),
+                                          (disc, T_I8)],
+                                   merge=MERGE_PRICE_DISCOUNT, layout=layout)
+        self.dims = []
+        for col in (d3_grp, d4_region):
+            ids = torch.arange(col.numel(), dtype=torch.int32, device=col.device)
+            self.dims.append(ctx.build_trie([ids], annos=[(col, T_I32)], merge=MERGE_FIRST, layout=layout))
+        self.nfact = int(keys[0].numel())
+        self.dim_sizes = [int(d3_grp.numel()), int(d4_region.numel())]
+
+    def query(self, order=(0, 1, 2, 3)):
+        edges = [{"slot": 0, "attrs": [0, 1, 2, 3], "anno": 0, "card": self.nfact},
+                 {"slot": 1, "attrs": [0], "card": 1},
+                 {"slot": 2, "attrs": [1], "card": 1},
+                 {"slot": 3, "attrs": [2], "card": self.dim_sizes[0]},
+                 {"slot": 4, "attrs": [3], "card": self.dim_sizes[1]}]
+        return make_query(4, edges, semiring=SUM_F32_KAHAN,
+                          group=[{"edge": 3, "anno": 0, "card": self.n_g1},
+                                 {"edge": 4, "anno": 0, "card": self.n_g2}])
+
+    def run(self, f1_trie, f2_trie, order=(0, 1, 2, 3)):
+        """Returns (group sums fp64, group counts, result view)."""
+        q = self.query(order)
+        plan = make_plan(list(order))
+        r = self.ctx.join_aggregate(q, plan, [self.fact, f1_trie, f2_trie] + self.dims)
+        v = r.wait()
+        gs, gc = r.groups()
+        r.free()
+        return gs, gc, v
+
+    def free(self):
+        self.fact.free()
+        for d in self.dims:
+            d.free()
+
+
+# ------------------------------------------------------ sparse LA helpers
+
+def spmv_query(nrows, x, card_a):
+    """y(i) = sum_j A(i,j) x(j): A in slot 0 (levels i, j), x completely dense."""
+    return make_query(2, [{"slot": 0, "attrs": [0, 1], "anno": 0, "card": card_a},
+                          {"slot": -1, "attrs": [1], "anno": 0, "flat": x}],
+                      semiring=SUMPROD_F32, group=[{"attr": 0, "card": nrows}], materialized=(0,))
+
+
+def spgemm_query(card_a, card_b):
+    """C(i,k) = sum_j A(i,j) B(j,k): A in slot 0 (i, j), B in slot 1 (j, k)."""
+    return make_query(3, [{"slot": 0, "attrs": [0, 1], "anno": 0, "card": card_a},
+                          {"slot": 1, "attrs": [1, 2], "anno": 0, "card": card_b}],
+                      semiring=SUMPROD_F32, group=[{"attr": 0, "card": 1}, {"attr": 2, "card": 1}],
+                      materialized=(0, 2))
+
+
+def matrix_trie(ctx, rows, cols, vals, layout=None):
+    return ctx.build_trie([rows, cols], key_order=[0, 1], annos=[(vals, T_F32)], merge=MERGE_SUM,
+                          layout=layout)

@@ -17,3 +17,20 @@ def orc():
     from oracle import oracle
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def lhlib():
+    from paper_1708_07859_b300 import build, lh
+    build.build()
+    return lh
+
+
+@pytest.fixture(scope="session")
+def ctx(lhlib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = lhlib.Context()
+    yield c
+    c.close()

@@ -1,0 +1,109 @@
+"""Sparse LA as join-aggregates on the GPU vs the fp64 oracle:
+SpMV y = A x (x completely dense) and SpGEMM C = A B in order [i, j, k];
+componentwise |c - c64| <= 1e-6 * sum |a b|, exact sparsity pattern."""
+import numpy as np
+import pytest
+
+from helpers import dev, dev_u32
+from paper_1708_07859_b300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+
+
+def build(ctx, lh, coo):
+    r, c, v = coo
+    return lh.matrix_trie(ctx, dev_u32(r), dev_u32(c), dev(v))
+
+
+def spmv(ctx, lh, coo, nrows, x):
+    t = build(ctx, lh, coo)
+    xd = dev(x)
+    q = lh.spmv_query(nrows, xd, coo[0].size)
+    r = ctx.join_aggregate(q, lh.make_plan([0, 1]), [t])
+    v = r.wait()
+    assert v.exec == lh.EXEC_SPMV
+    y = r.y()
+    r.free(); t.free()
+    return y
+
+
+@pytest.mark.parametrize("shape", [(300, 200, 7), (1000, 5000, 1), (64, 64, 64)])
+def test_spmv_small(ctx, orc, lhlib, shape):
+    n, m, k = shape
+    coo = gen.uniform_coo(n, m, k, 31)
+    x = gen.dense_vector(m, 32)
+    y = spmv(ctx, lhlib, coo, n, x)
+    w, wa = orc.spmv(*coo, n, x)
+    assert np.all(np.abs(y - w) <= TOL * wa + 1e-30)
+
+
+def test_spmv_identity_exact(ctx, lhlib):
+    n = 5000
+    x = gen.dense_vector(n, 3)
+    y = spmv(ctx, lhlib, (np.arange(n), np.arange(n), np.ones(n, np.float32)), n, x)
+    assert np.array_equal(y, x)
+
+
+def test_spmv_full_size(ctx, orc, lhlib):
+    n = 1 << 20
+    coo = gen.zipf_coo(n, n)
+    x = gen.dense_vector(n, gen.SEED_BASE + 20)
+    y = spmv(ctx, lhlib, coo, n, x)
+    w, wa = orc.spmv(*coo, n, x)
+    assert np.all(np.abs(y - w) <= TOL * wa + 1e-30)
+
+
+def spgemm(ctx, lh, A, B):
+    ta, tb = build(ctx, lh, A), build(ctx, lh, B)
+    q = lh.spgemm_query(A[0].size, B[0].size)
+    r = ctx.join_aggregate(q, lh.make_plan([0, 1, 2]), [ta, tb])
+    v = r.wait()
+    assert v.exec == lh.EXEC_SPGEMM
+    out = r.csr()
+    r.free(); ta.free(); tb.free()
+    return out
+
+
+def check_rows(orc, A, nA, B, nB, ncols, rows_ids, off, cols, vals, sel_idx):
+    sel = rows_ids[sel_idx]
+    woff, wcol, wval, wabs = orc.spgemm_rows(A, nA, B, nB, ncols, sel)
+    for s, p in enumerate(sel_idx):
+        g0, g1 = int(off[p]), int(off[p + 1])
+        w0, w1 = int(woff[s]), int(woff[s + 1])
+        assert np.array_equal(cols[g0:g1], wcol[w0:w1]), int(sel[s])
+        assert np.all(np.abs(vals[g0:g1] - wval[w0:w1]) <= TOL * wabs[w0:w1] + 1e-30)
+
+
+@pytest.mark.parametrize("shape", [(200, 150, 180, 5, 4), (100, 3000, 80, 40, 30), (50, 50, 50, 50, 50)])
+def test_spgemm_small(ctx, orc, lhlib, shape):
+    nA, nB, nC, ka, kb = shape
+    A = gen.uniform_coo(nA, nB, ka, 41)
+    B = gen.uniform_coo(nB, nC, kb, 42)
+    rows, off, cols, vals = spgemm(ctx, lhlib, A, B)
+    assert np.array_equal(rows, np.unique(A[0]))
+    check_rows(orc, A, nA, B, nB, nC, rows, off, cols, vals, np.arange(rows.size))
+
+
+def test_spgemm_identity_and_permutation_exact(ctx, lhlib):
+    A = gen.uniform_coo(300, 200, 9, 43)
+    I = (np.arange(200), np.arange(200), np.ones(200, np.float32))
+    rows, off, cols, vals = spgemm(ctx, lhlib, A, I)
+    for p, i in enumerate(rows):
+        m = A[0] == i
+        o = np.argsort(A[1][m])
+        assert np.array_equal(cols[off[p]:off[p + 1]], A[1][m][o])
+        assert np.array_equal(vals[off[p]:off[p + 1]], A[2][m][o])
+
+
+def test_spgemm_full_size_sampled_rows(ctx, orc, lhlib):
+    n = 1 << 20
+    A = gen.zipf_coo(n, n)
+    B = gen.zipf_coo(n, n, seed=gen.SEED_BASE + 12)
+    rows, off, cols, vals = spgemm(ctx, lhlib, A, B)
+    assert rows.size == n
+    rng = np.random.default_rng(0)
+    sel = np.unique(np.concatenate([rng.choice(n, 2000, replace=False), [0, 1, n - 1]]))
+    check_rows(orc, A, n, B, n, n, rows, off, cols, vals, sel)
+    # pattern sizes are bounded by 16 x 16 per row
+    assert int(np.max(np.diff(off.astype(np.int64)))) <= 256
