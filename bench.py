@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the join-aggregate hot path on one B300 (or N replicas).
+
+Workload: sparse linear algebra as join-aggregates (Section 4.1.2 / Section
+6.2.2 of the paper) -- A and B are 2^20 x 2^20 relations with 16 distinct
+columns per row drawn from Zipf(1.1), fp32 values U[-1, 1]; x is a completely
+dense fp32 relation.  One step is the whole path on one batch of inputs
+already resident in HBM: trie builds of A and B (radix sort, dedup, CSR
+levels, layouts), cost-based planning, y = A x (SpMV) and C = A B (SpGEMM in
+order [i, j, k] with the key GROUP BY), and -- when the build has it -- the
+dense 4096^3 block on tensor cores with one refinement step.
+
+Metric: join input elements per second (Gelem/s): per step, the SpMV reads
+nnz(A) set elements; the SpGEMM probes nnz(A) elements of A(i, .) against
+B's first level and unions sum_{(i,j) in A} |B(j)| elements into the GROUP BY.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ROWS = 1 << 20
+PER_ROW = 16
+DENSE = 4096
+METRIC = "WCOJ intersect Gelem/s & HBM GB/s; learned vs plain plan time at exact output"
+CONFIG_NAME = ("Sparse LA as join-aggregate: A, B 2^20x2^20 ~16 nnz/row Zipf(1.1) fp32; "
+               "y = A x and C = A B; dense 4096^3 BF16 block with FP64 refinement")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lh", choices=["lh", "reference"])
+    ap.add_argument("--rows", type=int, default=N_ROWS, help="rows/cols of A and B")
+    ap.add_argument("--no-dense", action="store_true", help="leave the dense block out of the step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    world, rank, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return world, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- inputs
+
+def make_inputs(n_rows, rank=0):
+    from paper_1708_07859_b300 import inputs as gen
+    A = gen.zipf_coo(n_rows, n_rows, PER_ROW, 1.1, gen.SEED_BASE + 2 + 100 * rank)
+    B = gen.zipf_coo(n_rows, n_rows, PER_ROW, 1.1, gen.SEED_BASE + 12 + 100 * rank)
+    x = gen.dense_vector(n_rows, gen.SEED_BASE + 20 + 100 * rank)
+    Dm = gen.dense_matrix(DENSE, DENSE, gen.SEED_BASE + 21 + 100 * rank)
+    Dn = gen.dense_matrix(DENSE, DENSE, gen.SEED_BASE + 22 + 100 * rank)
+    return A, B, x, Dm, Dn
+
+
+def step_elements(A, B):
+    """Join input elements of one step (independent of the plan)."""
+    brow = np.bincount(B[0].astype(np.int64), minlength=int(B[0].max()) + 1)
+    union = int(brow[A[1].astype(np.int64)].sum()) if A[1].size else 0
+    nnz = int(A[0].size)
+    return nnz + nnz + union, union
+
+
+# ---------------------------------------------------------------- the step
+
+class Step:
+    def __init__(self, ctx, lh, dev, with_dense):
+        self.ctx, self.lh, self.d = ctx, lh, dev
+        self.with_dense = with_dense
+        self.n = int(dev["x"].numel())
+
+    def run(self, keep=False):
+        lh, ctx, d = self.lh, self.ctx, self.d
+        ta = lh.matrix_trie(ctx, d["Ar"], d["Ac"], d["Av"])
+        tb = lh.matrix_trie(ctx, d["Br"], d["Bc"], d["Bv"])
+        q1 = lh.spmv_query(self.n, d["x"], int(d["Ar"].numel()))
+        p1 = ctx.plan(q1)
+        r1 = ctx.join_aggregate(q1, p1, [ta])
+        q2 = lh.spgemm_query(int(d["Ar"].numel()), int(d["Br"].numel()))
+        p2 = ctx.plan(q2)
+        r2 = ctx.join_aggregate(q2, p2, [ta, tb])
+        if self.with_dense:
+            ctx.dense_matmul(d["Dm"], d["Dn"], d["C32"], d["C64"])
+        out = (r1, r2, ta, tb)
+        if keep:
+            return out
+        for o in out:
+            o.free()
+        return None
+
+
+def flush_l2(buf):
+    buf.add_(1)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        self.index = ids[index] if index < len(ids) else str(index)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- roofline model
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), float(j.get("bf16_tflops", 1800.0)), \
+            float(j.get("bf16_tflops_sustained", 1400.0)), "measured"
+    return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+def algorithmic(kernel, n_rows, nnz_a, nnz_b, union, nnz_c):
+    """Algorithmic (compulsory) bytes or flops of one launch of `kernel` on
+    this workload: every input read once, every output written once."""
+    rows = n_rows
+    if kernel == "k_spgemm_numeric":
+        # A: row offsets, j and a; B: first-level bitset + rank, row offsets,
+        # k and b; the row results written once to the temporary (k, value)
+        b = 4 * (rows + 1) + 8 * nnz_a + 2 * (rows // 8) + 4 * (rows + 1) + 8 * nnz_b
+        return "hbm", b + 8 * nnz_c + 4 * rows
+    if kernel == "k_spmv":
+        return "hbm", 4 * rows + 4 * (rows + 1) + 8 * nnz_a + 4 * rows + 4 * rows
+    if kernel == "k_spgemm_gather":
+        return "hbm", 2 * 8 * nnz_c + 2 * 8 * (rows + 1)
+    if kernel == "k_spgemm_bound":
+        return "hbm", 4 * (rows + 1) + 4 * nnz_a + 2 * (rows // 8) + 4 * (rows + 1) + 4 * rows
+    if kernel == "k_sort_scatter":
+        return "hbm", 2 * 12 * nnz_a + 8 * 256 * ((nnz_a + 4095) // 4096)
+    if kernel == "k_sort_hist":
+        return "hbm", 8 * nnz_a
+    if kernel == "k_dense_gemm":
+        return "tensor", 3 * 2.0 * DENSE ** 3
+    return None, None
+
+
+# ------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(A, B, x, n_rows, target_s=15.0):
+    """The oracle as it stands, on a bounded sample: full SpMV plus the SpGEMM
+    rows of a sample of A, timed on all host cores."""
+    from oracle import oracle as orc
+    cores = orc.num_threads()
+    t0 = time.perf_counter()
+    orc.spmv(*A, n_rows, x)
+    t_spmv = time.perf_counter() - t0
+    brow = np.bincount(B[0].astype(np.int64), minlength=n_rows)
+    rows_per_a = np.bincount(A[0].astype(np.int64), minlength=n_rows)
+    # calibrate the row sample on a small slice, then size it for ~target_s
+    sel = np.arange(0, n_rows, max(1, n_rows // 4096), dtype=np.uint32)[:4096]
+    t0 = time.perf_counter()
+    orc.spgemm_rows(A, n_rows, B, n_rows, n_rows, sel)
+    t_cal = time.perf_counter() - t0
+    n_sel = int(min(n_rows, max(4096, 4096 * max(1.0, (target_s - t_spmv) / max(t_cal, 1e-3)) * 0.5)))
+    sel = np.linspace(0, n_rows - 1, n_sel).astype(np.uint32)
+    t0 = time.perf_counter()
+    orc.spgemm_rows(A, n_rows, B, n_rows, n_rows, sel)
+    t_gemm = time.perf_counter() - t0
+    # elements of the sample: SpMV over all of A, SpGEMM over the sampled rows
+    a_rows = A[0].astype(np.int64)
+    in_sel = np.zeros(n_rows, dtype=bool)
+    in_sel[sel] = True
+    m = in_sel[a_rows]
+    sample_union = int(brow[A[1][m].astype(np.int64)].sum())
+    elems = int(A[0].size) + int(rows_per_a[sel].sum()) + sample_union
+    secs = t_spmv + t_gemm
+    return {"value": elems / secs / 1e9, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+            "sample": f"full SpMV (nnz {A[0].size}) + SpGEMM rows of a {n_sel}-row sample of A "
+                      f"({secs:.1f} s of CPU work; trie build and dense block not in the sample)"}
+
+
+# ------------------------------------------------------------------- main
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if world > 1:
+        dist_init("gloo")
+    if rank != 0:
+        return 0
+    A, B, x, _, _ = make_inputs(args.rows)
+    vals = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(A, B, x, args.rows, target_s=6.0)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+        base = cb
+    v = statistics.mean(vals) if vals else base["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gelem/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIG_NAME, "rows": args.rows},
+            "cpu_baseline": dict(base, value=v),
+            "e2e": {"value": v, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist_init("nccl")
+    dev_id = torch.cuda.current_device()
+    from paper_1708_07859_b300 import lh
+
+    A, B, x, Dm, Dn = make_inputs(args.rows, rank)
+    elems, union = step_elements(A, B)
+    ctx = lh.Context()
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d = {"Ar": lh.to_device_u32(A[0]), "Ac": lh.to_device_u32(A[1]), "Av": to(A[2]),
+         "Br": lh.to_device_u32(B[0]), "Bc": lh.to_device_u32(B[1]), "Bv": to(B[2]), "x": to(x),
+         "Dm": to(Dm), "Dn": to(Dn),
+         "C32": torch.empty(DENSE, DENSE, dtype=torch.float32, device="cuda"),
+         "C64": torch.empty(DENSE, DENSE, dtype=torch.float64, device="cuda")}
+    with_dense = not args.no_dense
+    step = Step(ctx, lh, d, with_dense)
+    try:
+        step.run()
+    except lh.LHError as e:
+        if e.status != lh.EUNSUPPORTED or not with_dense:
+            raise
+        with_dense = False
+        step.with_dense = False
+    l2 = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
+
+    for _ in range(max(0, args.warmup)):
+        flush_l2(l2)
+        step.run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.trace_reset()
+    ctx.trace(True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_id) as clk:
+        for k in range(args.steps):
+            flush_l2(l2)
+            ev[k][0].record(stream)
+            step.run()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ctx.trace(False)
+    traces = ctx.trace_read()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), "cuda")
+    ms_per_step = total_ms / args.steps
+    all_elems = sum_over_ranks(elems * args.steps, "cuda")
+    value = all_elems / (total_ms / 1e3) / 1e9
+
+    # dominant kernel and its roofline
+    r1, r2, ta, tb = step.run(keep=True)
+    v2 = r2.wait()
+    nnz_c = int(v2.nnz)
+    for o in (r1, r2, ta, tb):
+        o.free()
+    hbm_peak, bf16_peak, bf16_sus, peak_kind = load_peaks()
+    launches = sum(v[0] for v in traces.values())
+    dom = max(traces.items(), key=lambda kv: kv[1][1])
+    name, (n_launch, tot) = dom
+    bound, alg = algorithmic(name, args.rows, int(A[0].size), int(B[0].size), union, nnz_c)
+    avg_ms = tot / max(1, n_launch)
+    if bound == "tensor":
+        achieved = alg / (avg_ms / 1e3) / 1e12
+        peak, unit = bf16_sus, "TFLOP/s"
+    elif bound == "hbm":
+        achieved = alg / (avg_ms / 1e3) / 1e9
+        peak, unit = hbm_peak, "GB/s"
+    else:
+        achieved, peak, unit = None, hbm_peak, "GB/s"
+    roof = {"kernel": name, "bound": bound or "hbm", "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json' if peak_kind == 'measured' else 'profiling recipe fallback'})",
+            "avg_launch_ms": avg_ms, "launches": n_launch,
+            "algorithmic_bytes_per_launch" if bound != "tensor" else "algorithmic_flops_per_launch": alg}
+    breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in
+                 sorted(traces.items(), key=lambda kv: -kv[1][1])[:8]}
+
+    # end to end through the public API: host (pinned) inputs -> step -> results on the host
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.cpu().pin_memory() for k, v in d.items() if k in ("Ar", "Ac", "Av", "Br", "Bc", "Bv", "x", "Dm", "Dn")}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        e2e_ms = []
+        d2h = 0
+        for k in range(args.steps):
+            flush_l2(l2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for key, hv in host.items():
+                d[key].copy_(hv, non_blocking=True)
+            r1, r2, ta, tb = step.run(keep=True)
+            v1 = r1.wait()
+            v2 = r2.wait()
+            y = r1.y()
+            rows_, off_, col_, val_ = r2.csr()
+            outs = [y, off_, col_, val_]
+            if with_dense:
+                c32 = d["C32"].cpu()
+                c64 = d["C64"].cpu()
+                outs += [c32.numpy(), c64.numpy()]
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            d2h = sum(o.nbytes for o in outs)
+            for o in (r1, r2, ta, tb):
+                o.free()
+        e_total = max_over_ranks(sum(e2e_ms), "cuda")
+        e2e = {"value": all_elems / (e_total / 1e3) / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e_total / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(A, B, x, args.rows)
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": CONFIG_NAME, "rows": args.rows, "nnz_per_row": PER_ROW,
+                           "zipf_s": 1.1, "dense": DENSE if with_dense else None,
+                           "step": "trie build A,B + plan + SpMV + SpGEMM" + (" + dense block" if with_dense else ""),
+                           "elements_per_step": elems, "nnz_c": nnz_c,
+                           "l2": "256 MB buffer written between timed steps; inputs 400 MB > L2",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "kernel_ms_per_step": breakdown}
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

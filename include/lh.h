@@ -80,6 +80,21 @@ const char *lh_version(void);
 lh_status lh_copy_d2h(lh_ctx *ctx, void *host, const void *dev, uint64_t bytes);
 lh_status lh_copy_h2d(lh_ctx *ctx, void *dev, const void *host, uint64_t bytes);
 
+/* Kernel tracing.  While enabled, every kernel this context launches is
+ * bracketed by two CUDA events recorded on the context stream (the stream it
+ * is launched on).  lh_trace_read waits for the stream and reports, per
+ * kernel name, the number of launches and the summed event time since the
+ * last lh_trace_reset; *n receives the number of names (entries beyond cap
+ * are not written). */
+typedef struct {
+    char name[40];
+    uint64_t launches;
+    double total_ms;
+} lh_trace_entry;
+lh_status lh_trace_enable(lh_ctx *ctx, int on);
+lh_status lh_trace_read(lh_ctx *ctx, lh_trace_entry *out, uint32_t cap, uint32_t *n);
+lh_status lh_trace_reset(lh_ctx *ctx);
+
 /* ------------------------------------------------------ tries (Section 2.2) */
 
 /* A relation as key columns and annotation columns (Section 2.1: keys join,

@@ -14,6 +14,8 @@ lh_status lh_fail(lh_ctx *ctx, lh_status s, const char *fmt, ...) {
     return s;
 }
 
+static void trace_fold(lh_ctx *ctx);
+
 extern "C" const char *lh_version(void) { return "lh-b300 0.1 (sm_103a)"; }
 
 extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
@@ -42,6 +44,8 @@ extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
 extern "C" lh_status lh_destroy(lh_ctx *ctx) {
     if (!ctx) return LH_EINVAL;
     cudaStreamSynchronize(ctx->stream);
+    trace_fold(ctx);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
@@ -83,6 +87,81 @@ extern "C" lh_status lh_copy_h2d(lh_ctx *ctx, void *dev, const void *host, uint6
     if (!bytes) return LH_OK;
     LH_CU(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
     LH_CU(cudaStreamSynchronize(ctx->stream));
+    return LH_OK;
+}
+
+// ------------------------------------------------------------------ tracing
+
+static cudaEvent_t pool_event(lh_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+LhTraceScope::LhTraceScope(lh_ctx *c, const char *name) : ctx(c), on(c && c->trace_on) {
+    if (!on) return;
+    rec.name = name;
+    rec.ev0 = pool_event(ctx);
+    rec.ev1 = pool_event(ctx);
+    cudaEventRecord(rec.ev0, ctx->stream);
+}
+
+LhTraceScope::~LhTraceScope() {
+    if (!on) return;
+    cudaEventRecord(rec.ev1, ctx->stream);
+    ctx->pending.push_back(rec);
+}
+
+static void trace_fold(lh_ctx *ctx) {
+    for (auto &r : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.ev0, r.ev1) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        auto &t = ctx->totals[r.name];
+        t.first += 1;
+        t.second += ms;
+        ctx->ev_pool.push_back(r.ev0);
+        ctx->ev_pool.push_back(r.ev1);
+    }
+    ctx->pending.clear();
+}
+
+extern "C" lh_status lh_trace_enable(lh_ctx *ctx, int on) {
+    if (!ctx) return LH_EINVAL;
+    ctx->trace_on = on != 0;
+    return LH_OK;
+}
+
+extern "C" lh_status lh_trace_read(lh_ctx *ctx, lh_trace_entry *out, uint32_t cap, uint32_t *n) {
+    if (!ctx || !n || (cap && !out)) return lh_fail(ctx, LH_EINVAL, "null argument");
+    LH_CU(cudaStreamSynchronize(ctx->stream));
+    trace_fold(ctx);
+    uint32_t k = 0;
+    for (auto &kv : ctx->totals) {
+        if (k < cap) {
+            memset(&out[k], 0, sizeof(out[k]));
+            strncpy(out[k].name, kv.first.c_str(), sizeof(out[k].name) - 1);
+            out[k].launches = kv.second.first;
+            out[k].total_ms = kv.second.second;
+        }
+        ++k;
+    }
+    *n = k;
+    return LH_OK;
+}
+
+extern "C" lh_status lh_trace_reset(lh_ctx *ctx) {
+    if (!ctx) return LH_EINVAL;
+    LH_CU(cudaStreamSynchronize(ctx->stream));
+    trace_fold(ctx);
+    ctx->totals.clear();
     return LH_OK;
 }
 
@@ -177,18 +256,18 @@ lh_status scan_impl(lh_ctx *ctx, const TI *in, TO *out, uint64_t n) {
     }
     uint64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 1) {
-        k_tile_scan<TI, TO><<<1, kScanThreads, 0, ctx->stream>>>(in, n, (const TO *)nullptr, out);
+        LH_TRACED(ctx, "k_tile_scan", k_tile_scan<TI, TO><<<1, kScanThreads, 0, ctx->stream>>>(in, n, (const TO *)nullptr, out));
         LH_LAUNCH_CHECK();
         return LH_OK;
     }
     TO *sums = nullptr, *pref = nullptr;
     LH_TRY(lh_alloc(ctx, &sums, tiles));
     LH_TRY(lh_alloc(ctx, &pref, tiles + 1));
-    k_tile_sums<TI, TO><<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, sums);
+    LH_TRACED(ctx, "k_tile_sums", k_tile_sums<TI, TO><<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, sums));
     LH_LAUNCH_CHECK();
     lh_status s = scan_impl<TO, TO>(ctx, sums, pref, tiles);
     if (s == LH_OK) {
-        k_tile_scan<TI, TO><<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, pref, out);
+        LH_TRACED(ctx, "k_tile_scan", k_tile_scan<TI, TO><<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, pref, out));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "scan: %s", cudaGetErrorString(e));
     }
@@ -303,11 +382,11 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes && s == LH_OK; ++p) {
         int shift = 8 * p;
-        k_sort_hist<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, n, shift, hist, ntiles);
+        LH_TRACED(ctx, "k_sort_hist", k_sort_hist<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, n, shift, hist, ntiles));
         s = lh_scan_u32_to_u64(ctx, hist, offs, (uint64_t)256 * ntiles);
         if (s != LH_OK) break;
-        k_sort_scatter<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, va, n, shift, offs, ntiles,
-                                                                  kb, vb);
+        LH_TRACED(ctx, "k_sort_scatter", k_sort_scatter<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, va, n, shift, offs, ntiles,
+                                                                  kb, vb));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort: %s", cudaGetErrorString(e));
         uint64_t *tk = ka; ka = kb; kb = tk;

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -19,6 +20,11 @@
 
 // ------------------------------------------------------------------ context
 
+struct lh_trace_rec {
+    const char *name;
+    cudaEvent_t ev0, ev1;
+};
+
 struct lh_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -27,7 +33,27 @@ struct lh_ctx {
     uint32_t *d_status = nullptr;   // first device-side error (lh_status), 0 = none
     uint64_t *h_pinned = nullptr;   // pinned host words for small read-backs
     static constexpr int kPinnedWords = 64;
+    // kernel tracing: CUDA events recorded on the launching stream around launches
+    bool trace_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<lh_trace_rec> pending;
+    std::map<std::string, std::pair<uint64_t, double>> totals;
 };
+
+// Scoped trace of one kernel launch (no-op unless tracing is on).
+struct LhTraceScope {
+    lh_ctx *ctx;
+    lh_trace_rec rec;
+    bool on;
+    LhTraceScope(lh_ctx *c, const char *name);
+    ~LhTraceScope();
+};
+
+#define LH_TRACED(ctx_, name_, ...)              \
+    do {                                         \
+        LhTraceScope lh_scope_((ctx_), (name_)); \
+        __VA_ARGS__;                             \
+    } while (0)
 
 lh_status lh_fail(lh_ctx *ctx, lh_status s, const char *fmt, ...);
 

@@ -220,7 +220,7 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
     if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)npairs + 1);
     if (s == LH_OK) {
         cudaMemsetAsync(counts, 0, npairs * sizeof(uint64_t), ctx->stream);
-        k_plan<<<lh_blocks(npairs, 256), 256, 0, ctx->stream>>>(npairs, a, b, plan, tiles);
+        LH_TRACED(ctx, "k_plan", k_plan<<<lh_blocks(npairs, 256), 256, 0, ctx->stream>>>(npairs, a, b, plan, tiles));
         s = lh_scan_u64_to_u64(ctx, tiles, off, npairs);
     }
     if (s == LH_OK) {
@@ -228,7 +228,7 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect, kThreads, 0);
         if (per_sm < 1) per_sm = 1;
         unsigned grid = (unsigned)(ctx->num_sms * per_sm);
-        k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, counts);
+        LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, counts));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "intersect: %s", cudaGetErrorString(e));
     }

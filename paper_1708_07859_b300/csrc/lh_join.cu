@@ -310,8 +310,8 @@ struct Driver {
         uint64_t total = 0;
         if (s == LH_OK) {
             unsigned g = (unsigned)std::min<uint64_t>(lh_blocks(nF, kThreads), (uint64_t)ctx->num_sms * 8);
-            k_sizes<<<g, kThreads, 0, ctx->stream>>>(q, d, posF, nF, capF, size, drvb,
-                                                     (unsigned long long *)r->d_elems);
+            LH_TRACED(ctx, "k_sizes", k_sizes<<<g, kThreads, 0, ctx->stream>>>(q, d, posF, nF, capF, size, drvb,
+                                                     (unsigned long long *)r->d_elems));
             s = lh_scan_u32_to_u64(ctx, size, off, nF);
         }
         if (s == LH_OK) s = lh_readback(ctx, off + nF, sizeof(uint64_t), &total);
@@ -325,9 +325,9 @@ struct Driver {
                 o.gsum = r->d_gsum;
                 o.gcount = (unsigned long long *)r->d_gcount;
                 if (mode_last == M_COUNT)
-                    k_expand<M_COUNT><<<grid_expand, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o);
+                    LH_TRACED(ctx, "k_expand", k_expand<M_COUNT><<<grid_expand, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o));
                 else
-                    k_expand<M_AGG><<<grid_expand, kThreads, smem_bytes, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o);
+                    LH_TRACED(ctx, "k_expand", k_expand<M_AGG><<<grid_expand, kThreads, smem_bytes, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o));
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e));
             }
@@ -348,7 +348,7 @@ struct Driver {
                     o.gvO = gvO;
                     o.counter = counter;
                     unsigned g = (unsigned)std::min<uint64_t>(lh_blocks(c1 - c0, kThreads), grid_expand);
-                    k_expand<M_EMIT><<<g, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, c0, c1, o);
+                    LH_TRACED(ctx, "k_expand", k_expand<M_EMIT><<<g, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, c0, c1, o));
                     cudaError_t e = cudaGetLastError();
                     if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e));
                 }

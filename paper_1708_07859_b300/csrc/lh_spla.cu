@@ -296,8 +296,8 @@ lh_status lh_run_spmv(lh_ctx *ctx, const lh_trie *a, const float *x, uint64_t x_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv, kSpmvThreads, 0);
     unsigned grid = std::min<unsigned>(lh_blocks((uint64_t)n0 * kSpmvGroup, kSpmvThreads),
                                        (unsigned)(ctx->num_sms * std::max(1, per_sm)));
-    k_spmv<<<grid, kSpmvThreads, 0, ctx->stream>>>(lh_trie_dview(a), (const float *)a->anno[0], x,
-                                                   (uint32_t)x_n, n0, r->y);
+    LH_TRACED(ctx, "k_spmv", k_spmv<<<grid, kSpmvThreads, 0, ctx->stream>>>(lh_trie_dview(a), (const float *)a->anno[0], x,
+                                                   (uint32_t)x_n, n0, r->y));
     LH_LAUNCH_CHECK();
     return LH_OK;
 }
@@ -325,8 +325,8 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
     STEP(lh_alloc(ctx, &gcap, n0));
     STEP(lh_alloc(ctx, &goff, (size_t)n0 + 1));
     if (s == LH_OK && n0) {
-        k_spgemm_bound<<<grid, T, 0, ctx->stream>>>(A, B, n0, ub);
-        k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(ub, n0, gcap);
+        LH_TRACED(ctx, "k_spgemm_bound", k_spgemm_bound<<<grid, T, 0, ctx->stream>>>(A, B, n0, ub));
+        LH_TRACED(ctx, "k_spgemm_gcap", k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(ub, n0, gcap));
     }
     STEP(lh_scan_u32_to_u64(ctx, ub, tmp_off, n0));
     STEP(lh_scan_u64_to_u64(ctx, gcap, goff, n0));
@@ -342,9 +342,9 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spgemm_numeric, kGemmThreads, 0);
         unsigned g2 = (unsigned)std::min<uint64_t>((n0 + kGemmWarps - 1) / kGemmWarps,
                                                    (uint64_t)ctx->num_sms * std::max(1, per_sm));
-        k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
+        LH_TRACED(ctx, "k_spgemm_numeric", k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
                                                                (const float *)b->anno[0], n0, tmp_off,
-                                                               goff, gkey, ghi, glo, tcol, tval, cnt);
+                                                               goff, gkey, ghi, glo, tcol, tval, cnt));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "spgemm: %s", cudaGetErrorString(e));
     }
@@ -356,7 +356,7 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         STEP(res_alloc(ctx, r, &r->c_val, nnz));
     }
     if (s == LH_OK && n0)
-        k_spgemm_gather<<<grid, T, 0, ctx->stream>>>(n0, tmp_off, r->c_off, tcol, tval, r->c_col, r->c_val);
+        LH_TRACED(ctx, "k_spgemm_gather", k_spgemm_gather<<<grid, T, 0, ctx->stream>>>(n0, tmp_off, r->c_off, tcol, tval, r->c_col, r->c_val));
 #undef STEP
     lh_free(ctx, ub); lh_free(ctx, cnt); lh_free(ctx, tmp_off); lh_free(ctx, gcap); lh_free(ctx, goff);
     lh_free(ctx, tcol); lh_free(ctx, tval); lh_free(ctx, gkey); lh_free(ctx, ghi); lh_free(ctx, glo);

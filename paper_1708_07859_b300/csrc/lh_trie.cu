@@ -300,8 +300,8 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
         if ((s = lh_alloc(ctx, &tmp_slot[l], L.nsets + 1)) != LH_OK) break;
         if ((s = lh_alloc(ctx, &tmp_words[l], L.nsets)) != LH_OK) break;
         if ((s = lh_alloc(ctx, &tmp_woff[l], L.nsets + 1)) != LH_OK) break;
-        k_layout_decide<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
-            L.vals, poffs, L.nsets, n0, t->bs_ratio, t->bs_min_card, tmp_isbs[l], tmp_words[l]);
+        LH_TRACED(ctx, "k_layout_decide", k_layout_decide<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
+            L.vals, poffs, L.nsets, n0, t->bs_ratio, t->bs_min_card, tmp_isbs[l], tmp_words[l]));
         if ((s = lh_scan_u32_to_u32(ctx, tmp_isbs[l], tmp_slot[l], L.nsets)) != LH_OK) break;
         if ((s = lh_scan_u64_to_u64(ctx, tmp_words[l], tmp_woff[l], L.nsets)) != LH_OK) break;
         uint32_t nbs = 0;
@@ -331,11 +331,11 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
         if ((s = trie_alloc(ctx, t, &L.bs_slot, L.nsets)) != LH_OK) break;
         if ((s = trie_alloc(ctx, t, &L.bs_meta, 4 * L.n_bs)) != LH_OK) break;
         if ((s = lh_alloc(ctx, &slot_set[l], L.n_bs)) != LH_OK) break;
-        k_layout_fill<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
+        LH_TRACED(ctx, "k_layout_fill", k_layout_fill<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
             L.vals, poffs, L.nsets, n0, tmp_isbs[l], tmp_slot[l], tmp_woff[l], level_word_base[l],
-            L.bs_slot, L.bs_meta, slot_set[l]);
-        k_layout_bits<<<lh_blocks(L.n_bs * 32, T, 1 << 16), T, 0, ctx->stream>>>(
-            L.vals, poffs, n0, L.bs_meta, slot_set[l], L.n_bs, t->words, t->rank);
+            L.bs_slot, L.bs_meta, slot_set[l]));
+        LH_TRACED(ctx, "k_layout_bits", k_layout_bits<<<lh_blocks(L.n_bs * 32, T, 1 << 16), T, 0, ctx->stream>>>(
+            L.vals, poffs, n0, L.bs_meta, slot_set[l], L.n_bs, t->words, t->rank));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "layout: %s", cudaGetErrorString(e));
     }
@@ -404,7 +404,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     if (s == LH_OK) {
         cudaMemsetAsync(d_max, 0, L * sizeof(uint32_t), ctx->stream);
         for (uint32_t l = 0; l < L && n; ++l)
-            k_col_max<<<G, T, 0, ctx->stream>>>(rel->keys[key_order[l]], n, d_max + l);
+            LH_TRACED(ctx, "k_col_max", k_col_max<<<G, T, 0, ctx->stream>>>(rel->keys[key_order[l]], n, d_max + l));
         uint32_t hmax[LH_MAX_LEVELS] = {0};
         STEP(lh_readback(ctx, d_max, L * sizeof(uint32_t), hmax));
         for (uint32_t l = 0; l < L; ++l) {
@@ -437,21 +437,21 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     STEP(lh_alloc(ctx, &flag, n));
     STEP(lh_alloc(ctx, &upos, n + 1));
     if (s == LH_OK && n) {
-        k_pack<<<G, T, 0, ctx->stream>>>(pa, n, key, rid);
+        LH_TRACED(ctx, "k_pack", k_pack<<<G, T, 0, ctx->stream>>>(pa, n, key, rid));
         STEP(lh_radix_sort_u64(ctx, key, rid, tkey, trid, n, (int)total_bits));
-        if (s == LH_OK) k_heads<<<G, T, 0, ctx->stream>>>(key, n, flag);
+        if (s == LH_OK) LH_TRACED(ctx, "k_heads", k_heads<<<G, T, 0, ctx->stream>>>(key, n, flag));
         STEP(lh_scan_u32_to_u64(ctx, flag, upos, n));
         STEP(lh_readback(ctx, upos + n, sizeof(uint64_t), &nu));
     }
     STEP(lh_alloc(ctx, &ukey, nu));
     STEP(lh_alloc(ctx, &runstart, nu));
-    if (s == LH_OK && n) k_compact_unique<<<G, T, 0, ctx->stream>>>(key, flag, upos, n, ukey, runstart);
+    if (s == LH_OK && n) LH_TRACED(ctx, "k_compact_unique", k_compact_unique<<<G, T, 0, ctx->stream>>>(key, flag, upos, n, ukey, runstart));
     // 3. levels
     for (uint32_t l = 0; l < L && s == LH_OK; ++l) {
         STEP(lh_alloc(ctx, &lflag[l], nu));
         STEP(lh_alloc(ctx, &lpos[l], nu + 1));
         if (s != LH_OK) break;
-        if (nu) k_level_flags<<<G, T, 0, ctx->stream>>>(ukey, nu, shift[l], lflag[l]);
+        if (nu) LH_TRACED(ctx, "k_level_flags", k_level_flags<<<G, T, 0, ctx->stream>>>(ukey, nu, shift[l], lflag[l]));
         STEP(lh_scan_u32_to_u32(ctx, lflag[l], lpos[l], nu));
         uint32_t nl = 0;
         STEP(lh_readback(ctx, lpos[l] + nu, sizeof(uint32_t), &nl));
@@ -465,10 +465,10 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     for (uint32_t l = 0; l < L && s == LH_OK; ++l) {
         uint64_t vmask = (bits[l] >= 64) ? ~0ull : ((1ull << bits[l]) - 1);
         if (nu)
-            k_level_emit<<<G, T, 0, ctx->stream>>>(
+            LH_TRACED(ctx, "k_level_emit", k_level_emit<<<G, T, 0, ctx->stream>>>(
                 ukey, nu, lflag[l], lpos[l], shift[l], vmask, t->lv[l].vals,
-                l ? lflag[l - 1] : nullptr, l ? lpos[l - 1] : nullptr, l ? t->lv[l - 1].offs : nullptr);
-        if (l + 1 < L) k_set_u32<<<1, 1, 0, ctx->stream>>>(t->lv[l].offs + t->lv[l].n, (uint32_t)t->lv[l + 1].n);
+                l ? lflag[l - 1] : nullptr, l ? lpos[l - 1] : nullptr, l ? t->lv[l - 1].offs : nullptr));
+        if (l + 1 < L) LH_TRACED(ctx, "k_set_u32", k_set_u32<<<1, 1, 0, ctx->stream>>>(t->lv[l].offs + t->lv[l].n, (uint32_t)t->lv[l + 1].n));
     }
     // 4. annotations in leaf order
     if (s == LH_OK && rel->nannos) {
@@ -499,7 +499,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
                 aa.out[c] = p;
             }
         }
-        if (s == LH_OK && nu) k_annos<<<G, T, 0, ctx->stream>>>(aa, rid, runstart, nu, n);
+        if (s == LH_OK && nu) LH_TRACED(ctx, "k_annos", k_annos<<<G, T, 0, ctx->stream>>>(aa, rid, runstart, nu, n));
     }
     if (s == LH_OK) {
         cudaError_t e = cudaGetLastError();
@@ -548,13 +548,13 @@ extern "C" lh_status lh_filter_trie(lh_ctx *ctx, const int32_t *col, uint64_t n,
     uint32_t *flag = nullptr, *pos = nullptr;
     lh_status s = lh_alloc(ctx, &flag, n);
     if (s == LH_OK) s = lh_alloc(ctx, &pos, n + 1);
-    if (s == LH_OK && n) k_filter_flags<<<G, T, 0, ctx->stream>>>(col, n, lo, hi, flag);
+    if (s == LH_OK && n) LH_TRACED(ctx, "k_filter_flags", k_filter_flags<<<G, T, 0, ctx->stream>>>(col, n, lo, hi, flag));
     if (s == LH_OK) s = lh_scan_u32_to_u32(ctx, flag, pos, n);
     uint32_t cnt = 0;
     if (s == LH_OK) s = lh_readback(ctx, pos + n, sizeof(uint32_t), &cnt);
     t->lv[0].n = cnt;
     if (s == LH_OK) s = trie_alloc(ctx, t, &t->lv[0].vals, cnt);
-    if (s == LH_OK && n) k_filter_emit<<<G, T, 0, ctx->stream>>>(flag, pos, n, t->lv[0].vals);
+    if (s == LH_OK && n) LH_TRACED(ctx, "k_filter_emit", k_filter_emit<<<G, T, 0, ctx->stream>>>(flag, pos, n, t->lv[0].vals));
     lh_free(ctx, flag);
     lh_free(ctx, pos);
     if (s == LH_OK) s = lh_trie_layout(ctx, t);

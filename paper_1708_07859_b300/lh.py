@@ -108,6 +108,10 @@ class ResultView(C.Structure):
                 ("elements", C.c_uint64)]
 
 
+class TraceEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
 class BatchQuery(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("graph", C.c_void_p)]
 
@@ -126,6 +130,9 @@ EXPORTS = {
     "lh_sync": [C.c_void_p],
     "lh_copy_d2h": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
     "lh_copy_h2d": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
+    "lh_trace_enable": [C.c_void_p, C.c_int],
+    "lh_trace_read": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
+    "lh_trace_reset": [C.c_void_p],
     "lh_build_trie": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "lh_filter_trie": [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p],
     "lh_trie_free": [C.c_void_p, C.c_void_p],
@@ -222,6 +229,20 @@ class Context:
 
     def sync(self):
         self._check(lib().lh_sync(self.h))
+
+    def trace(self, on=True):
+        self._check(lib().lh_trace_enable(self.h, 1 if on else 0))
+
+    def trace_reset(self):
+        self._check(lib().lh_trace_reset(self.h))
+
+    def trace_read(self):
+        """{kernel name: (launches, total ms)} since the last reset."""
+        n = C.c_uint32()
+        self._check(lib().lh_trace_read(self.h, None, 0, C.byref(n)))
+        arr = (TraceEntry * max(1, n.value))()
+        self._check(lib().lh_trace_read(self.h, arr, n.value, C.byref(n)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
 
     def set_stream(self, s):
         self.stream = s
