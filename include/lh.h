@@ -167,8 +167,9 @@ lh_status lh_trie_stats_get(lh_ctx *ctx, const lh_trie *t, lh_trie_stats *out);
  * entry in level l-1 (level 0 has one set, index 0).  The children of entry
  * p are vals_{l+1}[child_offs[p] .. child_offs[p+1]).  bs_slot[set] is the
  * set's bitset slot or 0xFFFFFFFF; bs_meta[4*slot + {0,1,2,3}] = {first
- * word, base value, word count, cardinality}; rank[w] = set bits before word
- * w inside its set. */
+ * word, base value, word count, rank base}; rank[w] = set bits of the whole
+ * bitset arena before word w, so the index of value v in its set is
+ * rank[w] - rank base + popc(word w below v's bit). */
 typedef struct {
     uint64_t n;
     uint64_t nsets;
@@ -206,6 +207,7 @@ typedef struct {
  * attribute). */
 lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
                                    const lh_set *b, uint64_t *counts);
+
 
 /* ----------------------------------------------- queries (Sections 2.3, 3.1) */
 

@@ -200,7 +200,7 @@ __device__ __forceinline__ bool lh_probe(const DTrie &T, int L, uint32_t set, ui
     if (lv.bs_slot != nullptr) {
         uint32_t slot = __ldg(lv.bs_slot + set);
         if (slot != LH_NOSLOT) {
-            uint4 m = __ldg(lv.bs_meta + slot);  // first word, base, words, card
+            uint4 m = __ldg(lv.bs_meta + slot);  // first word, base, words, rank base
             if (x < m.y) return false;
             uint32_t d = x - m.y;
             uint32_t w = d >> 5;
@@ -208,7 +208,7 @@ __device__ __forceinline__ bool lh_probe(const DTrie &T, int L, uint32_t set, ui
             uint32_t word = __ldg(T.words + m.x + w);
             uint32_t b = d & 31u;
             if (!((word >> b) & 1u)) return false;
-            *pos = lo + __ldg(T.rank + m.x + w) + __popc(word & ((1u << b) - 1u));
+            *pos = lo + (__ldg(T.rank + m.x + w) - m.w) + __popc(word & ((1u << b) - 1u));
             return true;
         }
     }

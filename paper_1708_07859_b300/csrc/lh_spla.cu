@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm_numeric(
     for (uint32_t p = gw; p < nA0; p += nw) {
         const uint64_t cap64 = goff[p + 1] - goff[p];
         const bool global = cap64 > 0;
+        // rows with at most kEscPairs products and 32 A entries go to k_spgemm_esc
+        if (!global && __ldg(A.lv[0].offs + p + 1) - __ldg(A.lv[0].offs + p) <= 32) continue;
         const uint32_t cap = global ? (uint32_t)cap64 : kTab;
         uint32_t *key = global ? gkey + goff[p] : S.key;
         float *th = global ? ghi + goff[p] : S.hi;
@@ -266,6 +268,160 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm_numeric(
     }
 }
 
+// ---- sort-based rows (expand, sort, compress) -------------------------------
+// A row with at most kEscPairs products: lane L expands products 8L..8L+7 of
+// the concatenated B rows into registers as 64-bit keys (k << 8 | product
+// index); a bitonic network over the 256 positions p = 8 * lane + e sorts
+// them (register compare-exchanges for distances < 8, shuffles for larger
+// ones); equal k are then adjacent and each run is summed with compensated
+// fp32 arithmetic and written once, already in ascending k.
+constexpr uint32_t kEscPairs = 256;
+constexpr int kEscWarps = 8;
+
+struct EscSmem {
+    float2 val[kEscPairs];
+    uint32_t skey[kEscPairs];
+    uint8_t sidx[kEscPairs];
+    uint32_t jb[32], jl[32], jp[32];
+    float ja[32];
+};
+
+template <int J>
+__device__ __forceinline__ void esc_intra(uint64_t (&key)[8], uint32_t lane, uint32_t k) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        if ((e & J) == 0) {
+            const bool up = (((lane << 3) + e) & k) == 0;
+            const uint64_t a = key[e], b = key[e + J];
+            const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+            key[e] = up ? lo : hi;
+            key[e + J] = up ? hi : lo;
+        }
+    }
+}
+
+__device__ __forceinline__ void esc_sort256(uint64_t (&key)[8], uint32_t lane) {
+    for (uint32_t k = 2; k <= kEscPairs; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 8) {
+                const uint32_t lj = j >> 3;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const bool up = (((lane << 3) + e) & k) == 0;
+                    const uint64_t other = __shfl_xor_sync(LH_FULL, key[e], lj);
+                    const bool keep_min = lower == up;
+                    key[e] = keep_min ? (key[e] < other ? key[e] : other) : (key[e] < other ? other : key[e]);
+                }
+            } else if (j == 4) {
+                esc_intra<4>(key, lane, k);
+            } else if (j == 2) {
+                esc_intra<2>(key, lane, k);
+            } else {
+                esc_intra<1>(key, lane, k);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
+    DTrie A, const float *av, DTrie B, const float *bv, uint32_t nA0, const uint32_t *ub,
+    const uint64_t *tmp_off, uint32_t *tcol, float *tval, uint32_t *cnt) {
+    __shared__ EscSmem sm_all[kEscWarps];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    EscSmem &S = sm_all[warp];
+    const uint32_t gw = blockIdx.x * kEscWarps + warp;
+    const uint32_t nw = gridDim.x * kEscWarps;
+    for (uint32_t p = gw; p < nA0; p += nw) {
+        const uint32_t alo = __ldg(A.lv[0].offs + p), ahi = __ldg(A.lv[0].offs + p + 1);
+        if (__ldg(ub + p) > kEscPairs || ahi - alo > 32) continue;
+        // stage the row's (j, a) with their B row ranges
+        const uint32_t q = alo + lane;
+        uint32_t bstart = 0, blen = 0;
+        float a = 0.f;
+        if (q < ahi) {
+            uint32_t pj;
+            if (lh_probe(B, 0, 0, 0, B.lv[0].n, __ldg(A.lv[1].vals + q), &pj)) {
+                bstart = __ldg(B.lv[0].offs + pj);
+                blen = __ldg(B.lv[0].offs + pj + 1) - bstart;
+                a = __ldg(av + q);
+            }
+        }
+        uint32_t incl = blen;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(LH_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        S.jb[lane] = bstart;
+        S.jl[lane] = blen;
+        S.jp[lane] = incl;
+        S.ja[lane] = a;
+        const uint32_t total = __shfl_sync(LH_FULL, incl, 31);
+        __syncwarp();
+        // expand: products 8 * lane + e
+        uint64_t key[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t t = (lane << 3) + e;
+            key[e] = ~0ull;
+            if (t < total) {
+                uint32_t lo = 0, hi = 31;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (S.jp[mid] > t) hi = mid;
+                    else lo = mid + 1;
+                }
+                const uint32_t pos = S.jb[lo] + (t - (S.jp[lo] - S.jl[lo]));
+                float ph, pl;
+                lh_two_prod(S.ja[lo], __ldg(bv + pos), ph, pl);
+                S.val[t] = make_float2(ph, pl);
+                key[e] = ((uint64_t)__ldg(B.lv[1].vals + pos) << 8) | t;
+            }
+        }
+        esc_sort256(key, lane);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t ps = (lane << 3) + e;
+            S.skey[ps] = (uint32_t)(key[e] >> 8);
+            S.sidx[ps] = (uint8_t)(key[e] & 255u);
+        }
+        __syncwarp();
+        // runs of equal k: the first position of a run sums it
+        uint32_t heads = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t ps = (lane << 3) + e;
+            heads += (ps < total && (ps == 0 || S.skey[ps] != S.skey[ps - 1])) ? 1u : 0u;
+        }
+        uint32_t hincl = heads;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(LH_FULL, hincl, o);
+            if (lane >= o) hincl += t;
+        }
+        uint32_t oi = hincl - heads;
+        const uint64_t t0 = tmp_off[p];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t ps = (lane << 3) + e;
+            if (ps < total && (ps == 0 || S.skey[ps] != S.skey[ps - 1])) {
+                const uint32_t kk = S.skey[ps];
+                float sh = 0.f, sl = 0.f;
+                for (uint32_t r = ps; r < total && S.skey[r] == kk; ++r) {
+                    const float2 v = S.val[S.sidx[r]];
+                    lh_pair_add(sh, sl, v.x, v.y);
+                }
+                tcol[t0 + oi] = kk;
+                tval[t0 + oi] = sh + sl;
+                ++oi;
+            }
+        }
+        if (lane == 31) cnt[p] = hincl;
+        __syncwarp();
+    }
+}
+
 __global__ void k_spgemm_gather(uint32_t nA0, const uint64_t *tmp_off, const uint64_t *c_off,
                                 const uint32_t *tcol, const float *tval, uint32_t *ccol, float *cval) {
     const int lane = threadIdx.x & 31;
@@ -342,6 +498,12 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spgemm_numeric, kGemmThreads, 0);
         unsigned g2 = (unsigned)std::min<uint64_t>((n0 + kGemmWarps - 1) / kGemmWarps,
                                                    (uint64_t)ctx->num_sms * std::max(1, per_sm));
+        int per_sm_e = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_e, k_spgemm_esc, kEscWarps * 32, 0);
+        unsigned g3 = (unsigned)std::min<uint64_t>((n0 + kEscWarps - 1) / kEscWarps,
+                                                   (uint64_t)ctx->num_sms * std::max(1, per_sm_e));
+        LH_TRACED(ctx, "k_spgemm_esc", k_spgemm_esc<<<g3, kEscWarps * 32, 0, ctx->stream>>>(
+            A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ub, tmp_off, tcol, tval, cnt));
         LH_TRACED(ctx, "k_spgemm_numeric", k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
                                                                (const float *)b->anno[0], n0, tmp_off,
                                                                goff, gkey, ghi, glo, tcol, tval, cnt));

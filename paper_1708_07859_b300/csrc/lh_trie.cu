@@ -204,38 +204,62 @@ __global__ void k_layout_fill(const uint32_t *vals, const uint32_t *poffs, uint6
     }
 }
 
-// One warp per bitset set: set the bits of its elements, then the per-word
-// exclusive rank (prefix popcount inside the set).
-__global__ void k_layout_bits(const uint32_t *vals, const uint32_t *poffs, uint32_t n0,
-                              const uint32_t *bs_meta, const uint32_t *slot_set, uint64_t n_bs,
-                              uint32_t *words, uint32_t *rank) {
-    const int lane = threadIdx.x & 31;
-    uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t slot = warp; slot < n_bs; slot += nwarps) {
-        uint32_t s = slot_set[slot];
-        uint32_t lo = poffs ? poffs[s] : 0, hi = poffs ? poffs[s + 1] : n0;
-        uint32_t w0 = bs_meta[4 * slot + 0], base = bs_meta[4 * slot + 1], nw = bs_meta[4 * slot + 2];
-        for (uint32_t q = lo + lane; q < hi; q += 32) {
-            uint32_t d = vals[q] - base;
-            atomicOr(&words[w0 + (d >> 5)], 1u << (d & 31u));
+// Bits of the bitset sets, element-parallel: every bitset set is cut into
+// chunks of kBitsChunk elements, one block per chunk, 8 consecutive elements
+// per thread; a thread ORs the bits that fall in one word and issues one
+// atomicOr per word it touches.
+constexpr uint32_t kBitsChunk = 2048;
+
+__global__ void k_layout_chunks(const uint32_t *bs_meta, uint64_t n_bs, uint32_t *chunks) {
+    for (uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < n_bs;
+         slot += (uint64_t)gridDim.x * blockDim.x)
+        chunks[slot] = (bs_meta[4 * slot + 3] + kBitsChunk - 1) / kBitsChunk;  // field 3 = card here
+}
+
+__global__ void __launch_bounds__(256) k_layout_bits(const uint32_t *vals, const uint32_t *poffs, uint32_t n0,
+                                                     const uint32_t *bs_meta, const uint32_t *slot_set,
+                                                     const uint32_t *chunk_off, uint32_t n_bs,
+                                                     uint32_t *words) {
+    const uint32_t total = chunk_off[n_bs];
+    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+        uint32_t lo_s = 0, hi_s = n_bs;  // chunk_off[lo_s] <= c < chunk_off[hi_s]
+        while (hi_s - lo_s > 1) {
+            uint32_t mid = (lo_s + hi_s) >> 1;
+            if (chunk_off[mid] <= c) lo_s = mid;
+            else hi_s = mid;
         }
-        __syncwarp();
-        __threadfence_block();
-        uint32_t carry = 0;
-        for (uint32_t c = 0; c < nw; c += 32) {
-            uint32_t w = c + lane;
-            uint32_t pc = (w < nw) ? __popc(__ldcg(words + w0 + w)) : 0u;
-            uint32_t incl = pc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(LH_FULL, incl, o);
-                if (lane >= o) incl += t;
+        const uint32_t slot = lo_s;
+        const uint32_t s = slot_set[slot];
+        const uint32_t lo = poffs ? poffs[s] : 0, hi = poffs ? poffs[s + 1] : n0;
+        const uint32_t w0 = bs_meta[4 * slot + 0], base = bs_meta[4 * slot + 1];
+        const uint32_t q0 = lo + (c - chunk_off[slot]) * kBitsChunk + threadIdx.x * 8;
+        const uint32_t q1 = min(q0 + 8, hi);
+        uint32_t cur = 0xFFFFFFFFu, mask = 0;
+        for (uint32_t q = q0; q < q1; ++q) {
+            const uint32_t d = vals[q] - base;
+            const uint32_t w = d >> 5;
+            if (w != cur) {
+                if (mask) atomicOr(&words[w0 + cur], mask);
+                cur = w;
+                mask = 0;
             }
-            if (w < nw) rank[w0 + w] = carry + incl - pc;
-            carry += __shfl_sync(LH_FULL, incl, 31);
+            mask |= 1u << (d & 31u);
         }
+        if (mask) atomicOr(&words[w0 + cur], mask);
     }
+}
+
+__global__ void k_popc_words(const uint32_t *words, uint64_t n, uint32_t *pc) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        pc[i] = __popc(words[i]);
+}
+
+// bs_meta field 3 <- rank of the set's first word (rank is arena-wide)
+__global__ void k_rank_base(uint32_t *bs_meta, uint64_t n_bs, const uint32_t *rank) {
+    for (uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < n_bs;
+         slot += (uint64_t)gridDim.x * blockDim.x)
+        bs_meta[4 * slot + 3] = rank[bs_meta[4 * slot + 0]];
 }
 
 }  // namespace
@@ -312,8 +336,9 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
         level_word_base[l] = total_words;
         total_words += nw;
     }
-    if (s == LH_OK && total_words >= (1ull << 32))
-        s = lh_fail(ctx, LH_EOVERFLOW, "bitset arena exceeds 2^32 words");
+    // ranks are 32-bit: the arena's bit count must stay below 2^32
+    if (s == LH_OK && total_words >= (1ull << 27))
+        s = lh_fail(ctx, LH_EOVERFLOW, "bitset arena exceeds 2^27 words");
     if (s == LH_OK && total_words > 0) {
         t->nwords = total_words;
         s = trie_alloc(ctx, t, &t->words, total_words);
@@ -334,10 +359,36 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
         LH_TRACED(ctx, "k_layout_fill", k_layout_fill<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
             L.vals, poffs, L.nsets, n0, tmp_isbs[l], tmp_slot[l], tmp_woff[l], level_word_base[l],
             L.bs_slot, L.bs_meta, slot_set[l]));
-        LH_TRACED(ctx, "k_layout_bits", k_layout_bits<<<lh_blocks(L.n_bs * 32, T, 1 << 16), T, 0, ctx->stream>>>(
-            L.vals, poffs, n0, L.bs_meta, slot_set[l], L.n_bs, t->words, t->rank));
+        uint32_t *chunks = nullptr, *coff = nullptr;
+        if ((s = lh_alloc(ctx, &chunks, L.n_bs)) != LH_OK) break;
+        if ((s = lh_alloc(ctx, &coff, L.n_bs + 1)) != LH_OK) { lh_free(ctx, chunks); break; }
+        LH_TRACED(ctx, "k_layout_chunks", k_layout_chunks<<<lh_blocks(L.n_bs, T, 1 << 16), T, 0, ctx->stream>>>(
+            L.bs_meta, L.n_bs, chunks));
+        s = lh_scan_u32_to_u32(ctx, chunks, coff, L.n_bs);
+        uint32_t nch = 0;
+        if (s == LH_OK) s = lh_readback(ctx, coff + L.n_bs, sizeof(uint32_t), &nch);
+        if (s == LH_OK && nch)
+            LH_TRACED(ctx, "k_layout_bits", k_layout_bits<<<std::min<uint32_t>(nch, (uint32_t)ctx->num_sms * 16), 256, 0, ctx->stream>>>(
+                L.vals, poffs, n0, L.bs_meta, slot_set[l], coff, (uint32_t)L.n_bs, t->words));
+        lh_free(ctx, chunks);
+        lh_free(ctx, coff);
         cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "layout: %s", cudaGetErrorString(e));
+        if (s == LH_OK && e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "layout: %s", cudaGetErrorString(e));
+    }
+    // arena-wide exclusive rank of every word, then each set's rank base
+    if (s == LH_OK && total_words > 0) {
+        uint32_t *pc = nullptr;
+        s = lh_alloc(ctx, &pc, total_words);
+        if (s == LH_OK) {
+            LH_TRACED(ctx, "k_popc_words", k_popc_words<<<lh_blocks(total_words, T, (uint32_t)ctx->num_sms * 16), T, 0, ctx->stream>>>(
+                t->words, total_words, pc));
+            s = lh_scan_u32_to_u32(ctx, pc, t->rank, total_words - 1);
+        }
+        lh_free(ctx, pc);
+        for (uint32_t l = 0; l < t->nlevels && s == LH_OK; ++l)
+            if (t->lv[l].n_bs)
+                LH_TRACED(ctx, "k_rank_base", k_rank_base<<<lh_blocks(t->lv[l].n_bs, T, 1 << 16), T, 0, ctx->stream>>>(
+                    t->lv[l].bs_meta, t->lv[l].n_bs, t->rank));
     }
     cleanup();
     return s;

@@ -26,13 +26,16 @@ def check_bitsets(tr, lv_index, arrays, words, rank):
             continue
         lo, hi = (0, lv["vals"].size) if lv_index == 0 else (int(prev["offs"][s]), int(prev["offs"][s + 1]))
         elems = lv["vals"][lo:hi].astype(np.int64)
-        w0, base, nw, card = (int(x) for x in lv["bs_meta"][slot])
-        assert card == hi - lo and base == (int(elems[0]) & ~127) and nw % 4 == 0 and w0 % 4 == 0
+        w0, base, nw, rbase = (int(x) for x in lv["bs_meta"][slot])
+        assert base == (int(elems[0]) & ~127) and nw % 4 == 0 and w0 % 4 == 0
         ws = words[w0:w0 + nw]
         bits = np.unpackbits(ws.view(np.uint8), bitorder="little").astype(bool)
         assert np.array_equal(np.flatnonzero(bits) + base, elems)
-        pc = np.array([bin(int(x)).count("1") for x in ws])
-        assert np.array_equal(rank[w0:w0 + nw], np.concatenate([[0], np.cumsum(pc)[:-1]]))
+        # arena-wide rank: bits of all earlier words; rank base = rank of the first word
+        all_pc = np.array([bin(int(x)).count("1") for x in words[:w0 + nw]], dtype=np.int64)
+        prefix = np.concatenate([[0], np.cumsum(all_pc)[:-1]])
+        assert rbase == prefix[w0]
+        assert np.array_equal(rank[w0:w0 + nw].astype(np.int64), prefix[w0:w0 + nw])
         checked += 1
     return checked
 
