@@ -208,6 +208,26 @@ typedef struct {
 lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
                                    const lh_set *b, uint64_t *counts);
 
+/* Same result as lh_intersect_count_batch, for callers that cannot allocate
+ * device memory while they run queries -- for instance a host application
+ * whose buffer pool or framework allocator owns all of the GPU's memory, or
+ * a latency-bound loop where an allocation could stall or fail.  The paper
+ * has no counterpart; this is a property of this library's interface.
+ *   - Allocates nothing: no cudaMalloc/cudaFree, no stream-ordered pool.
+ *     Its scratch (about 40 bytes per pair) lives in one fixed device array
+ *     sized for 65536 pairs (about 2.6 MB) that every GPU loading this
+ *     library holds until the process exits.
+ *   - npairs above 65536 is rejected with LH_EINVAL (counts untouched).
+ *   - The first call on a device looks the array's address up with that
+ *     device current (the context's device must be the current device);
+ *     make that first call before any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU (on
+ *     different streams, or from different contexts on one device) race and
+ *     give wrong counts; serialise them.
+ * a, b, counts: device arrays as for lh_intersect_count_batch; counts is
+ * zeroed, then written. */
+lh_status lh_intersect_count_batch_noalloc(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
+                                           const lh_set *b, uint64_t *counts);
 
 /* ----------------------------------------------- queries (Sections 2.3, 3.1) */
 

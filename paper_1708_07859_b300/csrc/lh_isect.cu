@@ -11,6 +11,8 @@
 //     binary-searched in the larger.
 //   uint cap bs: every uint element tests one bit.
 //   bs cap bs: 128-bit word AND + popc over the overlapping word range.
+#include <mutex>
+
 #include "lh_internal.cuh"
 
 namespace {
@@ -236,4 +238,122 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
     lh_free(ctx, tiles);
     lh_free(ctx, off);
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of lh_intersect_count_batch.
+//
+// Some callers cannot allocate device memory on their query path: a host
+// application whose buffer pool or framework allocator owns all of the
+// GPU's memory, or a latency-bound loop where an allocation could stall or
+// fail.  This entry point keeps its per-pair scratch (layout plan, tile
+// count, tile offset) in one file-scope device array instead of calling the
+// allocator.  The array holds kNoAllocMaxPairs pairs (about 2.6 MB) and stays
+// resident on every GPU that loads this library until the process exits.
+// All calls share it: calls whose work overlaps on the GPU (different
+// streams, or different contexts on one device) race on it.
+
+namespace {
+
+constexpr uint32_t kNoAllocMaxPairs = 65536;
+constexpr size_t kNaPlanBytes = sizeof(PairPlan) * kNoAllocMaxPairs;
+constexpr size_t kNaTilesBytes = sizeof(uint64_t) * kNoAllocMaxPairs;
+constexpr size_t kNaOffBytes = sizeof(uint64_t) * (kNoAllocMaxPairs + 1);
+constexpr size_t kNaPlanAt = 0;
+constexpr size_t kNaTilesAt = (kNaPlanAt + kNaPlanBytes + 255) & ~size_t(255);
+constexpr size_t kNaOffAt = (kNaTilesAt + kNaTilesBytes + 255) & ~size_t(255);
+constexpr size_t kNaBytes = kNaOffAt + kNaOffBytes;
+
+static __device__ __align__(256) unsigned char g_isect_scratch[kNaBytes];
+
+// Exclusive scan of n <= kNoAllocMaxPairs tile counts by one block of 1024
+// threads (the allocating path's multi-block scan needs temporaries).
+__global__ void __launch_bounds__(1024) k_scan_one_block(const uint64_t *in, uint32_t n, uint64_t *out) {
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < n; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = i < n ? in[i] : 0;
+        uint64_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t t = __shfl_up_sync(LH_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t w = warp_tot[lane], wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t t = __shfl_up_sync(LH_FULL, wi, o);
+                if (lane >= o) wi += t;
+            }
+            warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + warp_tot[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += warp_tot[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+std::mutex g_na_mu;
+constexpr int kNaMaxDevices = 64;
+unsigned char *g_na_ptr[kNaMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the context's device, looked up
+// once per device with that device current.
+lh_status noalloc_scratch(lh_ctx *ctx, unsigned char **out) {
+    int cur = -1;
+    LH_CU(cudaGetDevice(&cur));
+    if (cur != ctx->device)
+        return lh_fail(ctx, LH_EINVAL, "the context's device (%d) is not the current device (%d)", ctx->device, cur);
+    if (cur < 0 || cur >= kNaMaxDevices) return lh_fail(ctx, LH_EUNSUPPORTED, "device index %d", cur);
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_ptr[cur]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_isect_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return lh_fail(ctx, LH_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        }
+        g_na_ptr[cur] = (unsigned char *)p;
+    }
+    *out = g_na_ptr[cur];
+    return LH_OK;
+}
+
+}  // namespace
+
+extern "C" lh_status lh_intersect_count_batch_noalloc(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
+                                                      const lh_set *b, uint64_t *counts) {
+    if (!ctx) return LH_EINVAL;
+    if (npairs > kNoAllocMaxPairs)
+        return lh_fail(ctx, LH_EINVAL, "npairs %u exceeds the allocation-free limit of %u pairs", npairs,
+                       kNoAllocMaxPairs);
+    if (npairs == 0) return LH_OK;
+    if (!a || !b || !counts) return lh_fail(ctx, LH_EINVAL, "null argument");
+    unsigned char *scratch = nullptr;
+    LH_TRY(noalloc_scratch(ctx, &scratch));
+    PairPlan *plan = (PairPlan *)(scratch + kNaPlanAt);
+    uint64_t *tiles = (uint64_t *)(scratch + kNaTilesAt);
+    uint64_t *off = (uint64_t *)(scratch + kNaOffAt);
+    // counts start at zero: k_isect adds into them; plan, tiles and off are
+    // fully rewritten below for the first npairs pairs
+    LH_CU(cudaMemsetAsync(counts, 0, npairs * sizeof(uint64_t), ctx->stream));
+    LH_TRACED(ctx, "k_plan", k_plan<<<lh_blocks(npairs, 256), 256, 0, ctx->stream>>>(npairs, a, b, plan, tiles));
+    LH_TRACED(ctx, "k_scan_one_block", k_scan_one_block<<<1, 1024, 0, ctx->stream>>>(tiles, npairs, off));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)(ctx->num_sms * per_sm);
+    LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, counts));
+    LH_LAUNCH_CHECK();
+    return LH_OK;
 }

@@ -140,6 +140,7 @@ EXPORTS = {
     "lh_trie_level": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
     "lh_trie_anno": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p],
     "lh_intersect_count_batch": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_intersect_count_batch_noalloc": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_plan": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_edge_key_order": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
     "lh_join_aggregate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -282,6 +283,13 @@ class Context:
         """a_sets, b_sets: CUDA uint8 tensors holding packed lh_set arrays."""
         n = a_sets.numel() // C.sizeof(Set)
         self._check(lib().lh_intersect_count_batch(self.h, n, _ptr(a_sets), _ptr(b_sets), _ptr(counts)))
+
+    def intersect_count_batch_noalloc(self, a_sets, b_sets, counts, npairs=None):
+        """As intersect_count_batch, through the entry point that allocates no
+        device memory (at most 65536 pairs; see include/lh.h)."""
+        n = a_sets.numel() // C.sizeof(Set) if npairs is None else npairs
+        self._check(lib().lh_intersect_count_batch_noalloc(self.h, n, _ptr(a_sets), _ptr(b_sets),
+                                                           _ptr(counts)))
 
     # --- planning / joins ----------------------------------------------------
     def plan(self, q, kind=PLANNER_COST, model=None, rels=None, opts=None):
