@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="leave the dense block out of the step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--no-isect", action="store_true", help="skip the Figure 4a intersection batches")
     return ap.parse_args()
 
 
@@ -220,7 +221,7 @@ def algorithmic(kernel, n_rows, nnz_a, nnz_b, union, nnz_c):
     """Algorithmic (compulsory) bytes or flops of one launch of `kernel` on
     this workload: every input read once, every output written once."""
     rows = n_rows
-    if kernel == "k_spgemm_numeric":
+    if kernel in ("k_spgemm_numeric", "k_spgemm_esc"):
         # A: row offsets, j and a; B: first-level bitset + rank, row offsets,
         # k and b; the row results written once to the temporary (k, value)
         b = 4 * (rows + 1) + 8 * nnz_a + 2 * (rows // 8) + 4 * (rows + 1) + 8 * nnz_b
@@ -238,6 +239,66 @@ def algorithmic(kernel, n_rows, nnz_a, nnz_b, union, nnz_c):
     if kernel == "k_dense_gemm":
         return "tensor", 3 * 2.0 * DENSE ** 3
     return None, None
+
+
+# ------------------------------------------- intersection micro-benchmark
+
+def intersect_fig4a(ctx, lh, hbm_peak, reps=5, seed_base=0):
+    """Figure 4a shapes: batches of independent count-only intersections of
+    equal-cardinality sets in the three layout pairings (density 1/2), plus
+    sparse uint sets (density 1/32).  Reports elements/s, algorithmic GB/s of
+    the k_isect launches (sets read once) and the fraction of HBM peak."""
+    import torch
+    from paper_1708_07859_b300 import inputs as gen
+    out = {}
+    cases = [("uint_uint_sparse_1e6", 1_000_000, 32.0, 256, (0, 0)),
+             ("uint_uint_1e6", 1_000_000, 2.0, 256, (0, 0)),
+             ("uint_bs_1e6", 1_000_000, 2.0, 256, (0, 1)),
+             ("bs_bs_1e6", 1_000_000, 2.0, 256, (1, 1)),
+             ("uint_uint_sparse_1e7", 10_000_000, 32.0, 32, (0, 0)),
+             ("bs_bs_1e7", 10_000_000, 2.0, 32, (1, 1))]
+    for name, card, gap, npairs, (la, lb) in cases:
+        keep, da, db = [], [], []
+        nbytes = 0
+        for p in range(npairs):
+            for side, lay in ((0, la), (1, lb)):
+                v = gen.gap_set(card, gap, gen.SEED_BASE + 900000 + seed_base + 2 * p + side)
+                if lay == 0:
+                    t = lh.to_device_u32(v)
+                    d = (0, 0, v.size, t.data_ptr())
+                    nbytes += 4 * v.size
+                else:
+                    base = int(v[0]) & ~127
+                    nw = ((((int(v[-1]) - base) >> 5) + 1) + 3) & ~3
+                    dv = v.astype(np.int64) - base
+                    # distinct powers of two below 2^32 sum exactly in float64
+                    words = np.bincount(dv >> 5, weights=np.ldexp(1.0, (dv & 31).astype(np.int32)),
+                                        minlength=nw).astype(np.uint64).astype(np.uint32)
+                    t = lh.to_device_u32(words)
+                    d = (1, base, nw, t.data_ptr())
+                    nbytes += 4 * nw
+                keep.append(t)
+                (da if side == 0 else db).append(d)
+        A = torch.frombuffer(bytearray(lh.pack_sets(da)), dtype=torch.uint8).cuda()
+        B = torch.frombuffer(bytearray(lh.pack_sets(db)), dtype=torch.uint8).cuda()
+        counts = torch.zeros(npairs, dtype=torch.int64, device="cuda")
+        ctx.intersect_count_batch(A, B, counts)
+        torch.cuda.synchronize()
+        ctx.trace_reset()
+        ctx.trace(True)
+        for _ in range(reps):
+            ctx.intersect_count_batch(A, B, counts)
+        ctx.trace(False)
+        tr = ctx.trace_read()
+        n_l, tot = tr.get("k_isect", (0, 0.0))
+        ms = tot / max(1, n_l)
+        elems = 2 * card * npairs
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"pairs": npairs, "card": card, "ms": ms, "gelem_s": elems / (ms / 1e3) / 1e9,
+                     "alg_bytes": nbytes, "gb_s": gbs, "frac_hbm": gbs / hbm_peak}
+        del keep, A, B, counts
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------- CPU baseline
@@ -420,6 +481,8 @@ def main():
         e2e = {"value": all_elems / (e_total / 1e3) / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_total / args.steps}
 
+    fig4a = None if args.no_isect else intersect_fig4a(ctx, lh, hbm_peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(A, B, x, args.rows)
@@ -436,7 +499,7 @@ def main():
                            "l2": "256 MB buffer written between timed steps; inputs 400 MB > L2",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "kernel_ms_per_step": breakdown}
+                "clocks": clocks, "kernel_ms_per_step": breakdown, "intersect_fig4a": fig4a}
         print(json.dumps(line))
     ctx.close()
     if world > 1:

@@ -128,6 +128,7 @@ struct TrieLevel {
 struct lh_trie {
     uint32_t nlevels = 0;
     uint32_t key_order[LH_MAX_LEVELS] = {0};
+    uint32_t key_bits[LH_MAX_LEVELS] = {0};  // bits of the largest value per level
     uint64_t nrows_in = 0;
     TrieLevel lv[LH_MAX_LEVELS];
     uint32_t *words = nullptr;

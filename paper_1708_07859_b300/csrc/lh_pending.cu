@@ -11,9 +11,6 @@ lh_status lh_plan_exhaustive(lh_ctx *ctx, const lh_query *, const lh_relation_de
     return lh_fail(ctx, LH_EUNSUPPORTED, "exhaustive planner not built");
 }
 extern "C" {
-lh_status lh_dense_matmul(lh_ctx *ctx, const float *, const float *, int, int, int, float *, double *) {
-    return lh_fail(ctx, LH_EUNSUPPORTED, "dense block not built");
-}
 lh_status lh_batch_create(lh_ctx *ctx, uint32_t, const lh_batch_query *, const lh_batch_tuning *, uint64_t *, lh_batch **) {
     return lh_fail(ctx, LH_EUNSUPPORTED, "batch not built");
 }

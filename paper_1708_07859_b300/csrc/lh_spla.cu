@@ -280,50 +280,56 @@ constexpr int kEscWarps = 8;
 
 struct EscSmem {
     float2 val[kEscPairs];
-    uint32_t skey[kEscPairs];
-    uint8_t sidx[kEscPairs];
+    uint32_t skey[kEscPairs + kEscPairs / 32];
+    uint8_t sidx[kEscPairs + kEscPairs / 32];
     uint32_t jb[32], jl[32], jp[32];
     float ja[32];
 };
 
-template <int J>
-__device__ __forceinline__ void esc_intra(uint64_t (&key)[8], uint32_t lane, uint32_t k) {
+// Bitonic network over 256 keys held 8 per lane at positions p = 8 * lane + e,
+// fully unrolled so every distance and direction test is a constant:
+// distances below 8 are register compare-exchanges, larger ones shuffles.
+template <class K>
+__device__ __forceinline__ void esc_sort256(K (&key)[8], uint32_t lane) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        if ((e & J) == 0) {
-            const bool up = (((lane << 3) + e) & k) == 0;
-            const uint64_t a = key[e], b = key[e + J];
-            const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-            key[e] = up ? lo : hi;
-            key[e + J] = up ? hi : lo;
-        }
-    }
-}
-
-__device__ __forceinline__ void esc_sort256(uint64_t (&key)[8], uint32_t lane) {
-    for (uint32_t k = 2; k <= kEscPairs; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+    for (int kk = 1; kk <= 8; ++kk) {
+        const uint32_t k = 1u << kk;
+#pragma unroll
+        for (int jj = kk - 1; jj >= 0; --jj) {
+            const uint32_t j = 1u << jj;
             if (j >= 8) {
                 const uint32_t lj = j >> 3;
                 const bool lower = (lane & lj) == 0;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const bool up = (((lane << 3) + e) & k) == 0;
-                    const uint64_t other = __shfl_xor_sync(LH_FULL, key[e], lj);
-                    const bool keep_min = lower == up;
-                    key[e] = keep_min ? (key[e] < other ? key[e] : other) : (key[e] < other ? other : key[e]);
+                    const bool up = k >= 8 ? ((lane & (k >> 3)) == 0) : ((e & k) == 0);
+                    const K other = __shfl_xor_sync(LH_FULL, key[e], lj);
+                    const K mn = key[e] < other ? key[e] : other;
+                    const K mx = key[e] < other ? other : key[e];
+                    key[e] = (lower == up) ? mn : mx;
                 }
-            } else if (j == 4) {
-                esc_intra<4>(key, lane, k);
-            } else if (j == 2) {
-                esc_intra<2>(key, lane, k);
             } else {
-                esc_intra<1>(key, lane, k);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if ((e & j) == 0) {
+                        const bool up = k >= 8 ? ((lane & (k >> 3)) == 0) : ((e & k) == 0);
+                        const K x = key[e], y = key[e + j];
+                        const K mn = x < y ? x : y, mx = x < y ? y : x;
+                        key[e] = up ? mn : mx;
+                        key[e + j] = up ? mx : mn;
+                    }
+                }
             }
         }
     }
 }
 
+// shared index of sorted position p: one skew word per 32 so that lanes
+// reading p = 8 * lane + e hit distinct banks
+__device__ __forceinline__ uint32_t esc_sk(uint32_t p) { return p + (p >> 5); }
+
+// K = uint32_t when every k < 2^24 (k << 8 | index fits 32 bits), else uint64_t.
+template <class K>
 __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
     DTrie A, const float *av, DTrie B, const float *bv, uint32_t nA0, const uint32_t *ub,
     const uint64_t *tmp_off, uint32_t *tcol, float *tval, uint32_t *cnt) {
@@ -360,11 +366,11 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
         const uint32_t total = __shfl_sync(LH_FULL, incl, 31);
         __syncwarp();
         // expand: products 8 * lane + e
-        uint64_t key[8];
+        K key[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint32_t t = (lane << 3) + e;
-            key[e] = ~0ull;
+            key[e] = ~K(0);
             if (t < total) {
                 uint32_t lo = 0, hi = 31;
                 while (lo < hi) {
@@ -376,13 +382,13 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
                 float ph, pl;
                 lh_two_prod(S.ja[lo], __ldg(bv + pos), ph, pl);
                 S.val[t] = make_float2(ph, pl);
-                key[e] = ((uint64_t)__ldg(B.lv[1].vals + pos) << 8) | t;
+                key[e] = ((K)__ldg(B.lv[1].vals + pos) << 8) | t;
             }
         }
         esc_sort256(key, lane);
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const uint32_t ps = (lane << 3) + e;
+            const uint32_t ps = esc_sk((lane << 3) + e);
             S.skey[ps] = (uint32_t)(key[e] >> 8);
             S.sidx[ps] = (uint8_t)(key[e] & 255u);
         }
@@ -392,7 +398,7 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint32_t ps = (lane << 3) + e;
-            heads += (ps < total && (ps == 0 || S.skey[ps] != S.skey[ps - 1])) ? 1u : 0u;
+            heads += (ps < total && (ps == 0 || S.skey[esc_sk(ps)] != S.skey[esc_sk(ps - 1)])) ? 1u : 0u;
         }
         uint32_t hincl = heads;
 #pragma unroll
@@ -405,11 +411,11 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint32_t ps = (lane << 3) + e;
-            if (ps < total && (ps == 0 || S.skey[ps] != S.skey[ps - 1])) {
-                const uint32_t kk = S.skey[ps];
+            if (ps < total && (ps == 0 || S.skey[esc_sk(ps)] != S.skey[esc_sk(ps - 1)])) {
+                const uint32_t kk = S.skey[esc_sk(ps)];
                 float sh = 0.f, sl = 0.f;
-                for (uint32_t r = ps; r < total && S.skey[r] == kk; ++r) {
-                    const float2 v = S.val[S.sidx[r]];
+                for (uint32_t r = ps; r < total && S.skey[esc_sk(r)] == kk; ++r) {
+                    const float2 v = S.val[S.sidx[esc_sk(r)]];
                     lh_pair_add(sh, sl, v.x, v.y);
                 }
                 tcol[t0 + oi] = kk;
@@ -499,11 +505,17 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         unsigned g2 = (unsigned)std::min<uint64_t>((n0 + kGemmWarps - 1) / kGemmWarps,
                                                    (uint64_t)ctx->num_sms * std::max(1, per_sm));
         int per_sm_e = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_e, k_spgemm_esc, kEscWarps * 32, 0);
+        const bool narrow = b->key_bits[1] <= 24;  // every k < 2^24
+        if (narrow) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_e, k_spgemm_esc<uint32_t>, kEscWarps * 32, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_e, k_spgemm_esc<uint64_t>, kEscWarps * 32, 0);
         unsigned g3 = (unsigned)std::min<uint64_t>((n0 + kEscWarps - 1) / kEscWarps,
                                                    (uint64_t)ctx->num_sms * std::max(1, per_sm_e));
-        LH_TRACED(ctx, "k_spgemm_esc", k_spgemm_esc<<<g3, kEscWarps * 32, 0, ctx->stream>>>(
-            A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ub, tmp_off, tcol, tval, cnt));
+        if (narrow)
+            LH_TRACED(ctx, "k_spgemm_esc", k_spgemm_esc<uint32_t><<<g3, kEscWarps * 32, 0, ctx->stream>>>(
+                A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ub, tmp_off, tcol, tval, cnt));
+        else
+            LH_TRACED(ctx, "k_spgemm_esc", k_spgemm_esc<uint64_t><<<g3, kEscWarps * 32, 0, ctx->stream>>>(
+                A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ub, tmp_off, tcol, tval, cnt));
         LH_TRACED(ctx, "k_spgemm_numeric", k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
                                                                (const float *)b->anno[0], n0, tmp_off,
                                                                goff, gkey, ghi, glo, tcol, tval, cnt));

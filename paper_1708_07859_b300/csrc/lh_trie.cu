@@ -460,6 +460,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         STEP(lh_readback(ctx, d_max, L * sizeof(uint32_t), hmax));
         for (uint32_t l = 0; l < L; ++l) {
             bits[l] = hmax[l] ? 32 - __builtin_clz(hmax[l]) : 1;
+            t->key_bits[l] = bits[l];
             total_bits += bits[l];
         }
         if (s == LH_OK && total_bits > 64)
@@ -592,6 +593,7 @@ extern "C" lh_status lh_filter_trie(lh_ctx *ctx, const int32_t *col, uint64_t n,
     lh_trie *t = new lh_trie();
     t->nlevels = 1;
     t->nrows_in = n;
+    t->key_bits[0] = n > 1 ? 64 - __builtin_clzll(n - 1) : 1;
     t->bs_ratio = pol.bs_ratio;
     t->bs_min_card = pol.bs_min_card;
     const unsigned T = 256;

@@ -262,3 +262,15 @@ def sorted_set(card: int, span: int, seed: int):
             v = np.union1d(v, rng.integers(0, span, size=card))
         v = np.sort(rng.choice(v, size=card, replace=False))
     return v.astype(np.uint32)
+
+
+def gap_set(card: int, mean_gap: float, seed: int, start: int = 0):
+    """``card`` distinct sorted uint32 values whose consecutive gaps are
+    Geometric(1/mean_gap): a uniform random set of density ~1/mean_gap.
+    Cheap enough to draw hundreds of million-element sets."""
+    rng = _rng(seed)
+    gaps = rng.geometric(1.0 / mean_gap, size=card)
+    v = start + np.cumsum(gaps) - gaps[0]
+    if v.size and v[-1] >= (1 << 32):
+        raise ValueError("set exceeds the uint32 domain")
+    return v.astype(np.uint32)
