@@ -432,6 +432,14 @@ lh_status lh_model_adam_step(lh_ctx *ctx, lh_model *m, float lr, float beta1, fl
 lh_status lh_model_train(lh_ctx *ctx, lh_model *m, const float *X, const float *y, uint32_t n,
                          uint32_t epochs, uint32_t batch, float lr, uint64_t seed,
                          float *final_loss);
+/* Engine-measured time of q under plan on `tries` (as for
+ * lh_join_aggregate): one warm-up run, then the mean of `repeats` runs
+ * timed with CUDA events on the context stream, into *ms (host).  With
+ * budget_ms > 0 the generic driver stops issuing chunks once a run exceeds
+ * the budget and the call returns LH_ETIMEOUT (the planner's training data
+ * and exhaustive judge rank such plans last). */
+lh_status lh_plan_time(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan, lh_trie *const *tries,
+                       float budget_ms, uint32_t repeats, float *ms);
 /* Planner features (host float[LH_NFEAT]) of running q under plan on
  * `tries` (built for that plan).  Computed on the device from the tries'
  * level statistics. */

@@ -106,24 +106,48 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *red) {
     return t;  // valid in thread 0
 }
 
+// pair of a global tile: last p with tile_off[p] <= tile
+__device__ __forceinline__ uint32_t tile_pair(const uint64_t *tile_off, uint32_t npairs, uint64_t tile) {
+    uint32_t lo = 0, hi = npairs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (tile_off[mid] <= tile) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Merge-path split of every merge tile's first diagonal, all tiles at once
+// (the kernel below then starts loading immediately).
+__global__ void k_isect_splits(uint32_t npairs, const lh_set *A, const lh_set *B, const PairPlan *plan,
+                               const uint64_t *tile_off, uint64_t *split) {
+    const uint64_t total = tile_off[npairs];
+    for (uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; tile < total;
+         tile += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = tile_pair(tile_off, npairs, tile);
+        const PairPlan pl = plan[p];
+        if (pl.kind != K_MERGE) continue;
+        lh_set a = A[p], b = B[p];
+        if (pl.swap) { lh_set x = a; a = b; b = x; }
+        split[tile] = mp_split(a.data, a.n, b.data, b.n, (tile - tile_off[p]) * kTile);
+    }
+}
+
+// split: per-tile merge-path starts from k_isect_splits, or null to compute
+// them here (the allocation-free entry point has no room for them)
 __global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_set *A,
                                                     const lh_set *B, const PairPlan *plan,
-                                                    const uint64_t *tile_off, uint64_t *counts) {
+                                                    const uint64_t *tile_off, const uint64_t *split,
+                                                    uint64_t *counts) {
     __shared__ uint32_t sa[kTile];
     __shared__ uint32_t sb[kTile + 1];
-    __shared__ uint64_t bounds[4];
+    __shared__ uint64_t bounds[2];
     __shared__ uint32_t red[kThreads / 32];
     const uint64_t total = tile_off[npairs];
     for (uint64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        // pair of this tile
-        uint32_t lo = 0, hi = npairs;
-        while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (tile_off[mid] <= tile) lo = mid;
-            else hi = mid;
-        }
-        const uint32_t p = lo;
+        const uint32_t p = tile_pair(tile_off, npairs, tile);
         const uint64_t t = tile - tile_off[p];
+        const uint64_t ntp = tile_off[p + 1] - tile_off[p];
         const PairPlan pl = plan[p];
         lh_set a = A[p], b = B[p];
         if (pl.swap) { lh_set x = a; a = b; b = x; }
@@ -131,22 +155,37 @@ __global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_se
         if (pl.kind == K_MERGE) {
             const uint64_t nd = a.n + b.n;
             const uint64_t d0 = t * kTile, d1 = min(nd, d0 + kTile);
-            if (threadIdx.x == 0) {
-                uint64_t i0 = mp_split(a.data, a.n, b.data, b.n, d0);
-                bounds[0] = i0;
-                bounds[1] = d0 - i0;
-            } else if (threadIdx.x == 32) {
-                uint64_t i1 = mp_split(a.data, a.n, b.data, b.n, d1);
-                bounds[2] = i1;
-                bounds[3] = d1 - i1;
+            uint64_t i0, i1;
+            if (split) {
+                i0 = split[tile];
+                i1 = (t + 1 < ntp) ? split[tile + 1] : a.n;
+            } else {
+                if (threadIdx.x == 0) bounds[0] = mp_split(a.data, a.n, b.data, b.n, d0);
+                else if (threadIdx.x == 32) bounds[1] = mp_split(a.data, a.n, b.data, b.n, d1);
+                __syncthreads();
+                i0 = bounds[0];
+                i1 = bounds[1];
             }
-            __syncthreads();
-            const uint64_t i0 = bounds[0], j0 = bounds[1], i1 = bounds[2], j1 = bounds[3];
+            const uint64_t j0 = d0 - i0, j1 = d1 - i1;
             const uint32_t la = (uint32_t)(i1 - i0), lb = (uint32_t)(j1 - j0);
             const bool has_ext = j1 < b.n;
-            for (uint32_t k = threadIdx.x; k < la; k += kThreads) sa[k] = __ldg(a.data + i0 + k);
-            for (uint32_t k = threadIdx.x; k < lb + (has_ext ? 1u : 0u); k += kThreads)
-                sb[k] = __ldg(b.data + j0 + k);
+            const uint32_t lbx = lb + (has_ext ? 1u : 0u);
+            // all loads of this thread in flight before any shared store
+            uint32_t ra[kItems], rb[kItems + 1];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                ra[r] = k < la ? __ldg(a.data + i0 + k) : 0u;
+                rb[r] = k < lbx ? __ldg(b.data + j0 + k) : 0u;
+            }
+            rb[kItems] = (threadIdx.x == 0 && kTile < lbx) ? __ldg(b.data + j0 + kTile) : 0u;
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                if (k < la) sa[k] = ra[r];
+                if (k < lbx) sb[k] = rb[r];
+            }
+            if (threadIdx.x == 0 && kTile < lbx) sb[kTile] = rb[kItems];
             __syncthreads();
             const uint32_t s = threadIdx.x * kItems;
             const uint32_t e = min(s + kItems, la + lb);
@@ -166,30 +205,42 @@ __global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_se
             }
         } else if (pl.kind == K_PROBE) {
             const uint64_t base = t * kTile;
-            for (uint32_t k = threadIdx.x; k < kTile; k += kThreads) {
-                uint64_t i = base + k;
-                if (i >= a.n) break;
-                uint32_t x = __ldg(a.data + i);
+            uint32_t x[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint64_t i = base + threadIdx.x + r * kThreads;
+                x[r] = i < a.n ? __ldg(a.data + i) : 0u;
+            }
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint64_t i = base + threadIdx.x + r * kThreads;
+                if (i >= a.n) continue;
                 uint64_t l = 0, h = b.n;
                 while (l < h) {
                     uint64_t m = (l + h) >> 1;
-                    if (__ldg(b.data + m) < x) l = m + 1;
+                    if (__ldg(b.data + m) < x[r]) l = m + 1;
                     else h = m;
                 }
-                cnt += (l < b.n && __ldg(b.data + l) == x) ? 1u : 0u;
+                cnt += (l < b.n && __ldg(b.data + l) == x[r]) ? 1u : 0u;
             }
         } else if (pl.kind == K_UBS) {
             const uint64_t base = t * kTile;
-            for (uint32_t k = threadIdx.x; k < kTile; k += kThreads) {
-                uint64_t i = base + k;
-                if (i >= a.n) break;
-                uint32_t x = __ldg(a.data + i);
-                if (x >= b.base) {
-                    uint32_t d = x - b.base;
-                    uint64_t w = d >> 5;
-                    if (w < b.n) cnt += (__ldg(b.data + w) >> (d & 31u)) & 1u;
-                }
+            uint32_t x[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint64_t i = base + threadIdx.x + r * kThreads;
+                x[r] = i < a.n ? __ldg(a.data + i) : b.base - 1u;  // padding: below the base when base > 0
             }
+            uint32_t w[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint64_t i = base + threadIdx.x + r * kThreads;
+                const uint32_t d = x[r] - b.base;
+                const bool in = i < a.n && x[r] >= b.base && (uint64_t)(d >> 5) < b.n;
+                w[r] = in ? __ldg(b.data + (d >> 5)) : 0u;
+            }
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((x[r] - b.base) & 31u)) & 1u;
         } else if (pl.kind == K_BB) {
             // word ranges start on 128-bit boundaries (bases are multiples of
             // 128 values = 4 words), so uint4 loads are aligned
@@ -208,6 +259,178 @@ __global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_se
     }
 }
 
+// ---- descriptor-driven variant (allocating entry point) ---------------------
+// Everything a tile needs -- its pair, slice pointers and lengths -- is
+// computed for all tiles at once by k_isect_tiles, so a CTA's only dependent
+// load per tile is its 48-byte descriptor, and the next tile's data loads are
+// issued into registers before the current tile is merged.
+
+struct __align__(16) TileDesc {
+    const uint32_t *a;   // merge: A slice; probe / ubs: uint elements; bs: A words
+    const uint32_t *b;   // merge: B slice; probe: B set; ubs: B words; bs: B words
+    uint32_t la, lb;     // merge: slice lengths; probe / ubs: elements; bs: words
+    uint32_t pair, kind; // kind | 256 when the merge slice of B has one extra head element
+    uint64_t bn;         // probe: |B|; ubs: B words
+    uint32_t bbase, pad; // ubs: B base value
+};
+
+__global__ void k_isect_tiles(uint32_t npairs, const lh_set *A, const lh_set *B, const PairPlan *plan,
+                              const uint64_t *tile_off, TileDesc *desc) {
+    const uint64_t total = tile_off[npairs];
+    for (uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; tile < total;
+         tile += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = tile_pair(tile_off, npairs, tile);
+        const uint64_t t = tile - tile_off[p];
+        const PairPlan pl = plan[p];
+        lh_set a = A[p], b = B[p];
+        if (pl.swap) { lh_set x = a; a = b; b = x; }
+        TileDesc d;
+        d.pair = p;
+        d.kind = pl.kind;
+        d.bn = 0;
+        d.bbase = 0;
+        d.pad = 0;
+        if (pl.kind == K_MERGE) {
+            const uint64_t nd = a.n + b.n;
+            const uint64_t d0 = t * kTile, d1 = min(nd, d0 + kTile);
+            const uint64_t i0 = mp_split(a.data, a.n, b.data, b.n, d0);
+            const uint64_t i1 = mp_split(a.data, a.n, b.data, b.n, d1);
+            const uint64_t j0 = d0 - i0, j1 = d1 - i1;
+            d.a = a.data + i0;
+            d.b = b.data + j0;
+            d.la = (uint32_t)(i1 - i0);
+            d.lb = (uint32_t)(j1 - j0);
+            if (j1 < b.n) d.kind |= 256u;
+        } else if (pl.kind == K_BB) {
+            const uint64_t w0 = pl.lo_w + t * kTile, w1 = min(pl.hi_w, w0 + kTile);
+            d.a = a.data + (w0 - (a.base >> 5));
+            d.b = b.data + (w0 - (b.base >> 5));
+            d.la = d.lb = (uint32_t)(w1 - w0);
+        } else {  // probe or uint cap bs: a tile of the uint side
+            const uint64_t i0 = t * kTile;
+            d.a = a.data + i0;
+            d.la = (uint32_t)min((uint64_t)kTile, a.n - i0);
+            d.b = b.data;
+            d.lb = 0;
+            d.bn = b.n;
+            d.bbase = b.base;
+        }
+        desc[tile] = d;
+    }
+}
+
+__device__ __forceinline__ void prefetch_tile(const TileDesc &d, uint32_t (&ra)[kItems], uint32_t (&rb)[kItems + 1]) {
+    const uint32_t kind = d.kind & 255u;
+    if (kind == K_MERGE) {
+        const uint32_t lbx = d.lb + ((d.kind >> 8) & 1u);
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const uint32_t k = threadIdx.x + r * kThreads;
+            ra[r] = k < d.la ? __ldg(d.a + k) : 0u;
+            rb[r] = k < lbx ? __ldg(d.b + k) : 0u;
+        }
+        rb[kItems] = (threadIdx.x == 0 && (uint32_t)kTile < lbx) ? __ldg(d.b + kTile) : 0u;
+    } else if (kind == K_PROBE || kind == K_UBS) {
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const uint32_t k = threadIdx.x + r * kThreads;
+            ra[r] = k < d.la ? __ldg(d.a + k) : 0u;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_isect2(const TileDesc *desc, uint64_t total, uint64_t *counts) {
+    __shared__ uint32_t sa[kTile];
+    __shared__ uint32_t sb[kTile + 1];
+    __shared__ uint32_t red[kThreads / 32];
+    uint32_t ra[kItems], rb[kItems + 1];
+    uint64_t tile = blockIdx.x;
+    if (tile >= total) return;
+    TileDesc d = desc[tile];
+    prefetch_tile(d, ra, rb);
+    while (tile < total) {
+        const uint32_t kind = d.kind & 255u;
+        const bool has_ext = (d.kind >> 8) & 1u;
+        const uint32_t la = d.la, lb = d.lb, pair = d.pair;
+        uint32_t cnt = 0;
+        if (kind == K_MERGE) {
+            const uint32_t lbx = lb + (has_ext ? 1u : 0u);
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                if (k < la) sa[k] = ra[r];
+                if (k < lbx) sb[k] = rb[r];
+            }
+            if (threadIdx.x == 0 && (uint32_t)kTile < lbx) sb[kTile] = rb[kItems];
+        }
+        // the next tile's descriptor and data loads go out before this tile's work
+        uint32_t xa[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) xa[r] = ra[r];
+        const uint64_t next = tile + gridDim.x;
+        TileDesc nd = d;
+        if (next < total) {
+            nd = desc[next];
+            prefetch_tile(nd, ra, rb);
+        }
+        __syncthreads();
+        if (kind == K_MERGE) {
+            const uint32_t s = threadIdx.x * kItems;
+            const uint32_t e = min(s + kItems, la + lb);
+            if (s < e) {
+                uint32_t ii = sm_split(sa, la, sb, lb, s);
+                uint32_t jj = s - ii;
+                for (uint32_t step = s; step < e; ++step) {
+                    if (ii < la && (jj >= lb || sa[ii] <= sb[jj])) {
+                        const uint32_t av = sa[ii];
+                        const bool head = jj < lb || (jj == lb && has_ext);
+                        if (head && sb[jj] == av) ++cnt;
+                        ++ii;
+                    } else {
+                        ++jj;
+                    }
+                }
+            }
+        } else if (kind == K_UBS) {
+            uint32_t w[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                const uint32_t dd = xa[r] - d.bbase;
+                const bool in = k < la && xa[r] >= d.bbase && (uint64_t)(dd >> 5) < d.bn;
+                w[r] = in ? __ldg(d.b + (dd >> 5)) : 0u;
+            }
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((xa[r] - d.bbase) & 31u)) & 1u;
+        } else if (kind == K_PROBE) {
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                if (k >= la) continue;
+                uint64_t l = 0, h = d.bn;
+                while (l < h) {
+                    const uint64_t m = (l + h) >> 1;
+                    if (__ldg(d.b + m) < xa[r]) l = m + 1;
+                    else h = m;
+                }
+                cnt += (l < d.bn && __ldg(d.b + l) == xa[r]) ? 1u : 0u;
+            }
+        } else if (kind == K_BB) {
+            const uint4 *pa = (const uint4 *)d.a;
+            const uint4 *pb = (const uint4 *)d.b;
+            const uint32_t nv = la >> 2;
+            for (uint32_t k = threadIdx.x; k < nv; k += kThreads) {
+                const uint4 x = __ldg(pa + k), y = __ldg(pb + k);
+                cnt += __popc(x.x & y.x) + __popc(x.y & y.y) + __popc(x.z & y.z) + __popc(x.w & y.w);
+            }
+        }
+        const uint32_t tot = block_sum(cnt, red);  // ends with a barrier: shared tiles are free again
+        if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + pair), (unsigned long long)tot);
+        tile = next;
+        d = nd;
+    }
+}
+
 }  // namespace
 
 extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
@@ -217,6 +440,7 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
     if (!a || !b || !counts) return lh_fail(ctx, LH_EINVAL, "null argument");
     PairPlan *plan = nullptr;
     uint64_t *tiles = nullptr, *off = nullptr;
+    uint64_t ntiles = 0;
     lh_status s = lh_alloc(ctx, &plan, npairs);
     if (s == LH_OK) s = lh_alloc(ctx, &tiles, npairs);
     if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)npairs + 1);
@@ -225,18 +449,24 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
         LH_TRACED(ctx, "k_plan", k_plan<<<lh_blocks(npairs, 256), 256, 0, ctx->stream>>>(npairs, a, b, plan, tiles));
         s = lh_scan_u64_to_u64(ctx, tiles, off, npairs);
     }
-    if (s == LH_OK) {
+    if (s == LH_OK) s = lh_readback(ctx, off + npairs, sizeof(uint64_t), &ntiles);
+    TileDesc *desc = nullptr;
+    if (s == LH_OK) s = lh_alloc(ctx, &desc, ntiles);
+    if (s == LH_OK && ntiles) {
+        LH_TRACED(ctx, "k_isect_tiles", k_isect_tiles<<<lh_blocks(ntiles, 256, (unsigned)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+                                            npairs, a, b, plan, off, desc));
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect2, kThreads, 0);
         if (per_sm < 1) per_sm = 1;
-        unsigned grid = (unsigned)(ctx->num_sms * per_sm);
-        LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, counts));
+        unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * per_sm);
+        LH_TRACED(ctx, "k_isect", k_isect2<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "intersect: %s", cudaGetErrorString(e));
     }
     lh_free(ctx, plan);
     lh_free(ctx, tiles);
     lh_free(ctx, off);
+    lh_free(ctx, desc);
     return s;
 }
 
@@ -353,7 +583,7 @@ extern "C" lh_status lh_intersect_count_batch_noalloc(lh_ctx *ctx, uint32_t npai
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect, kThreads, 0);
     if (per_sm < 1) per_sm = 1;
     unsigned grid = (unsigned)(ctx->num_sms * per_sm);
-    LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, counts));
+    LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, nullptr, counts));
     LH_LAUNCH_CHECK();
     return LH_OK;
 }

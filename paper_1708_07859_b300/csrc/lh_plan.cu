@@ -110,7 +110,7 @@ void lh_candidate_orders(const lh_query *q, std::vector<std::vector<uint32_t>> &
     } while (std::next_permutation(mat.begin(), mat.end()));
 }
 
-static uint32_t exec_for(const lh_query *q, const uint32_t *order) {
+uint32_t lh_exec_for(const lh_query *q, const uint32_t *order) {
     // mirrors the pattern checks of the join dispatcher
     if (q->exec != LH_EXEC_AUTO) return q->exec;
     if (q->n_edges == 2 && q->n_group == 1 && q->group[0].anno < 0 && q->n_attrs == 2) {
@@ -145,7 +145,7 @@ lh_status lh_plan_cost(lh_ctx *ctx, const lh_query *q, const uint64_t *cards, lh
     for (uint32_t i = 0; i < q->n_attrs; ++i) out->order[i] = bo[i];
     out->cost = best;
     out->bs_ratio = 32;
-    out->exec = exec_for(q, out->order);
+    out->exec = lh_exec_for(q, out->order);
     out->predicted_log_ms = NAN;
     out->measured_ms = NAN;
     out->n_candidates = (uint32_t)cands.size();

@@ -5,6 +5,7 @@
 
 #include "lh_internal.cuh"
 
+uint32_t lh_exec_for(const lh_query *q, const uint32_t *order);
 int lh_icost_vertex(const lh_query *q, const uint32_t *order, uint32_t i);
 void lh_weights(const lh_query *q, const uint64_t *cards, int64_t *w);
 int64_t lh_cost_of(const lh_query *q, const uint32_t *order, const int64_t *w);

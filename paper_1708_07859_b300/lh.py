@@ -160,6 +160,7 @@ EXPORTS = {
     "lh_model_train": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32,
                        C.c_uint32, C.c_float, C.c_uint64, C.c_void_p],
     "lh_plan_features": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_plan_time": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_uint32, C.c_void_p],
 }
 
 _lib = None
@@ -497,6 +498,43 @@ class GraphJoin:
         self.query = make_query(self.n_attrs, [{"slot": 0, "attrs": list(p), "card": card}
                                                for p in self.pattern])
 
+    def rel(self):
+        """lh_relation_desc of E(src, dst) (for the learned / exhaustive planners)."""
+        if not hasattr(self, "_rel"):
+            self._rel = relation_desc([self.src, self.dst])
+        return self._rel
+
+    def plan(self, kind=PLANNER_COST, model=None, opts=None):
+        return self.ctx.plan(self.query, kind, model, [self.rel()] * self.query.n_edges, opts)
+
+    def time_plan(self, plan, budget_ms=0.0, repeats=1):
+        """Engine-measured ms of this query under plan (None if over budget)."""
+        tries, q = self._bind(plan, (plan.bs_ratio, 32 if plan.bs_ratio else 0))
+        arr = (C.c_void_p * max(1, len(tries)))(*[t.h.value for t in tries])
+        ms = C.c_float()
+        st = lib().lh_plan_time(self.ctx.h, C.byref(q), C.byref(plan), arr, budget_ms, repeats, C.byref(ms))
+        if st == ETIMEOUT:
+            return None
+        self.ctx._check(st)
+        return float(ms.value)
+
+    def features(self, plan):
+        tries, q = self._bind(plan, (plan.bs_ratio, 32 if plan.bs_ratio else 0))
+        return plan_features(self.ctx, q, plan, tries)
+
+    def _bind(self, plan, layout=None):
+        tries = []
+        q = Query()
+        C.memmove(C.byref(q), C.byref(self.query), C.sizeof(Query))
+        slots = {}
+        for e in range(q.n_edges):
+            ko = tuple(self.ctx.edge_key_order(self.query, plan, e))
+            if ko not in slots:
+                slots[ko] = len(tries)
+                tries.append(self.trie(ko, layout))
+            q.edges[e].trie_slot = slots[ko]
+        return tries, q
+
     def trie(self, key_order, layout=None):
         lay = tuple(layout or self.layout)
         k = (tuple(key_order), lay)
@@ -505,18 +543,8 @@ class GraphJoin:
         return self.tries[k]
 
     def run(self, plan, layout=None):
-        """Returns (count, elements, result view) under ``plan``."""
-        tries = []
-        q = Query()
-        C.memmove(C.byref(q), C.byref(self.query), C.sizeof(Query))
-        slots = {}
-        for e in range(q.n_edges):
-            ko = self.ctx.edge_key_order(self.query, plan, e)
-            key = tuple(ko)
-            if key not in slots:
-                slots[key] = len(tries)
-                tries.append(self.trie(ko, layout))
-            q.edges[e].trie_slot = slots[key]
+        """Returns (count, elements) under ``plan``."""
+        tries, q = self._bind(plan, layout)
         r = self.ctx.join_aggregate(q, plan, tries)
         v = r.wait()
         out = (int(v.count), int(v.elements))
@@ -600,3 +628,147 @@ def spgemm_query(card_a, card_b):
 def matrix_trie(ctx, rows, cols, vals, layout=None):
     return ctx.build_trie([rows, cols], key_order=[0, 1], annos=[(vals, T_F32)], merge=MERGE_SUM,
                           layout=layout)
+
+
+# ---------------------------------------------------------- batched joins
+
+class Batch:
+    """One persistent, graph-captured launch over many triangle / 4-clique
+    COUNT queries (lh_batch_*).  queries: list of (kind, edge Trie built with
+    key order [0, 1])."""
+
+    def __init__(self, ctx, queries, tuning=None):
+        import torch
+        self.ctx = ctx
+        self.n = len(queries)
+        self.queries = queries
+        arr = (BatchQuery * self.n)(*[BatchQuery(k, t.h.value) for k, t in queries])
+        self.counts = torch.zeros(self.n, dtype=torch.int64, device="cuda")
+        tun = BatchTuning(*tuning) if tuning is not None else None
+        self.h = C.c_void_p()
+        ctx._check(lib().lh_batch_create(ctx.h, self.n, arr, C.byref(tun) if tun is not None else None,
+                                         _ptr(self.counts), C.byref(self.h)))
+
+    def run(self):
+        self.ctx._check(lib().lh_batch_run(self.ctx.h, self.h))
+
+    def result(self):
+        self.ctx.sync()
+        return self.counts.cpu().numpy().astype(np.uint64)
+
+    def free(self):
+        if self.h:
+            lib().lh_batch_free(self.ctx.h, self.h)
+            self.h = C.c_void_p()
+
+
+def batch_autotune(ctx, queries):
+    """(t_warp, chunk, ctas_per_sm), best replay ms."""
+    import torch
+    n = len(queries)
+    arr = (BatchQuery * n)(*[BatchQuery(k, t.h.value) for k, t in queries])
+    counts = torch.zeros(n, dtype=torch.int64, device="cuda")
+    best = BatchTuning()
+    ms = C.c_float()
+    ctx._check(lib().lh_batch_autotune(ctx.h, n, arr, _ptr(counts), C.byref(best), C.byref(ms)))
+    return (best.t_warp, best.chunk, best.ctas_per_sm), float(ms.value)
+
+
+# ------------------------------------------------------ learned cost model
+
+def relation_desc(keys, annos=()):
+    """lh_relation_desc for CUDA key columns (and (tensor, dtype) annotations)."""
+    d = RelationDesc()
+    d.nrows = int(keys[0].numel()) if keys else 0
+    d.nkeys = len(keys)
+    for i, k in enumerate(keys):
+        d.keys[i] = k.data_ptr()
+    d.nannos = len(annos)
+    for i, (t, ty) in enumerate(annos):
+        d.annos[i] = t.data_ptr()
+        d.anno_types[i] = ty
+    return d
+
+
+class Model:
+    """The planner MLP (NFEAT -> hidden -> hidden -> 1) living on the device."""
+
+    def __init__(self, ctx, n_in=NFEAT, hidden=64, seed=0):
+        self.ctx, self.n_in, self.hidden = ctx, n_in, hidden
+        self.h = C.c_void_p()
+        ctx._check(lib().lh_model_create(ctx.h, n_in, hidden, seed, C.byref(self.h)))
+        p, g, n = C.c_void_p(), C.c_void_p(), C.c_uint64()
+        ctx._check(lib().lh_model_buffers(ctx.h, self.h, C.byref(p), C.byref(g), C.byref(n)))
+        self._p, self._g, self.n_params = p.value, g.value, int(n.value)
+
+    def params(self):
+        return _dev_to_np(self._p, self.n_params, np.float32, self.ctx)
+
+    def grads(self):
+        return _dev_to_np(self._g, self.n_params, np.float32, self.ctx)
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.n_params
+        self.ctx._check(lib().lh_copy_h2d(self.ctx.h, C.c_void_p(self._p), C.c_void_p(a.ctypes.data), a.nbytes))
+
+    def forward(self, X):
+        import torch
+        out = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        self.ctx._check(lib().lh_model_forward(self.ctx.h, self.h, _ptr(X), X.shape[0], _ptr(out)))
+        return out
+
+    def loss_grad(self, X, y):
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.ctx._check(lib().lh_model_loss_grad(self.ctx.h, self.h, _ptr(X), _ptr(y), X.shape[0], _ptr(loss)))
+        return float(loss.item())
+
+    def adam_step(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.ctx._check(lib().lh_model_adam_step(self.ctx.h, self.h, lr, b1, b2, eps))
+
+    def train(self, X, y, epochs=100, batch=256, lr=1e-3, seed=0):
+        out = C.c_float()
+        self.ctx._check(lib().lh_model_train(self.ctx.h, self.h, _ptr(X), _ptr(y), X.shape[0], epochs, batch, lr,
+                                             seed, C.byref(out)))
+        return float(out.value)
+
+    def save(self, path):
+        np.save(path, self.params())
+
+    def load(self, path):
+        self.set_params(np.load(path))
+
+    def free(self):
+        if self.h:
+            lib().lh_model_free(self.ctx.h, self.h)
+            self.h = C.c_void_p()
+
+
+def unpack_params(flat, n_in, hidden):
+    """Flat parameter vector -> dict W1, b1, W2, b2, W3, b3 (header layout)."""
+    o = 0
+    out = {}
+    for name, shape in (("W1", (n_in, hidden)), ("b1", (hidden,)), ("W2", (hidden, hidden)), ("b2", (hidden,)),
+                        ("W3", (hidden, 1)), ("b3", (1,))):
+        n = int(np.prod(shape))
+        out[name] = np.asarray(flat[o:o + n]).reshape(shape)
+        o += n
+    return out
+
+
+def plan_features(ctx, q, plan, tries):
+    f = (C.c_float * NFEAT)()
+    arr = (C.c_void_p * max(1, len(tries)))(*[t.h.value for t in tries])
+    ctx._check(lib().lh_plan_features(ctx.h, C.byref(q), C.byref(plan), arr, f))
+    return np.array(f[:], dtype=np.float32)
+
+
+def plan_opts(policies=(0, 8, 32, 128), budget_ms=0.0, repeats=1):
+    o = PlanOpts()
+    o.n_policies = len(policies)
+    for i, p in enumerate(policies):
+        o.policies[i] = p
+    o.time_budget_ms = budget_ms
+    o.repeats = repeats
+    return o

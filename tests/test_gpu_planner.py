@@ -1,0 +1,69 @@
+"""Planner on the GPU: the cost model's choices (Section 4), features of
+candidate plans, the exhaustive judge and a learned model all yield plans
+whose results equal the oracle's."""
+import itertools
+
+import numpy as np
+import pytest
+
+from helpers import dev_u32
+from paper_1708_07859_b300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+
+def test_cost_planner_sparse_la_orders(ctx, lhlib):
+    lh = lhlib
+    import torch
+    x = torch.zeros(100, device="cuda")
+    q = lh.spgemm_query(1600, 1600)
+    p = ctx.plan(q)
+    assert p.order_list() == [0, 1, 2] and p.exec == lh.EXEC_SPGEMM      # relaxed order, Section 4.1.2
+    q = lh.spmv_query(100, x, 1600)
+    p = ctx.plan(q)
+    assert p.order_list() == [0, 1] and p.exec == lh.EXEC_SPMV
+
+
+def test_features_layout(ctx, lhlib):
+    lh = lhlib
+    s, d = gen.gnm_edges(300, 3000, 3)
+    g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), "triangle")
+    p = lh.make_plan([2, 0, 1], bs_ratio=8)
+    f = g.features(p)
+    assert f.shape == (lh.NFEAT,)
+    assert np.allclose(f[:3], np.log2(3001.0), atol=1e-4) and np.all(f[3:6] == 0)
+    onehot = f[31:56].reshape(5, 5)
+    assert onehot[0, 2] == 1 and onehot[1, 0] == 1 and onehot[2, 1] == 1 and onehot.sum() == 3
+    assert f[56:60].tolist() == [0, 1, 0, 0]
+    # first attribute: one first-level set per relation -> quantiles of one set size
+    assert f[6 + 3] >= f[6 + 0]
+    g.free()
+
+
+@pytest.mark.parametrize("shape", ["triangle", "cycle4", "lollipop"])
+def test_exhaustive_and_cost_plans_give_oracle_counts(ctx, orc, lhlib, shape):
+    lh = lhlib
+    s, d = gen.chung_lu_edges(3000, 20000, 2.2, 11)
+    want = orc.GRAPH_COUNT[shape](s, d)
+    g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), shape)
+    pc = g.plan()
+    assert g.run(pc, layout=(pc.bs_ratio, 32))[0] == want
+    pe = g.plan(lh.PLANNER_EXHAUSTIVE, opts=lh.plan_opts((0, 32), budget_ms=2000.0))
+    assert pe.n_candidates == 2 * len(list(itertools.permutations(range(g.n_attrs))))
+    assert np.isfinite(pe.measured_ms) and pe.measured_ms > 0
+    assert g.run(pe, layout=(pe.bs_ratio, 32 if pe.bs_ratio else 0))[0] == want
+    g.free()
+
+
+def test_learned_planner_returns_valid_plan(ctx, orc, lhlib):
+    lh = lhlib
+    s, d = gen.gnm_edges(500, 5000, 13)
+    want = orc.cycle4_count(s, d)
+    g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), "cycle4")
+    m = lh.Model(ctx, lh.NFEAT, 64, seed=4)
+    pl = g.plan(lh.PLANNER_LEARNED, model=m, opts=lh.plan_opts((0, 32)))
+    assert sorted(pl.order_list()) == [0, 1, 2, 3] and np.isfinite(pl.predicted_log_ms)
+    assert pl.n_candidates == 48
+    assert g.run(pl, layout=(pl.bs_ratio, 32 if pl.bs_ratio else 0))[0] == want
+    m.free()
+    g.free()
