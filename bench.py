@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-isect", action="store_true", help="skip the Figure 4a intersection batches")
+    ap.add_argument("--isect-only", action="store_true", help="run only the Figure 4a intersection batches")
+    ap.add_argument("--no-extras", action="store_true", help="skip the planner and batched-launch comparisons")
+    ap.add_argument("--extras-only", action="store_true", help="run only the planner and batched comparisons")
     return ap.parse_args()
 
 
@@ -301,6 +304,76 @@ def intersect_fig4a(ctx, lh, hbm_peak, reps=5, seed_base=0):
     return out
 
 
+# ------------------------------------------------ planner and batched extras
+
+def planner_compare(ctx, lh, edges=1 << 20, n=1 << 17, seed_off=7):
+    """Learned vs cost-model vs exhaustive-best plan times (ms, engine
+    events) for the 4-cycle and lollipop COUNT joins over one Chung-Lu graph;
+    the three plans must return identical counts."""
+    from paper_1708_07859_b300 import inputs as gen
+    from paper_1708_07859_b300 import planner
+    s, d = gen.chung_lu_edges(n, edges, 2.1, gen.SEED_BASE + seed_off)
+    model = planner.load_model(ctx)
+    out = {"graph": {"kind": "chung_lu", "n": n, "m": edges, "beta": 2.1}}
+    for shape in ("cycle4", "lollipop"):
+        r = planner.compare(ctx, model, shape, s, d, budget_ms=500.0, repeats=3)
+        out[shape] = {k: r[k] for k in ("cost", "learned", "best", "identical_counts", "regret_learned",
+                                        "regret_cost", "learned_plan_s", "exhaustive_plan_s")}
+    model.free()
+    return out
+
+
+def batched_compare(ctx, lh, count=1024):
+    """One persistent graph-captured launch over `count` triangle / 4-clique
+    COUNT queries (log-uniform 100..1e5 edges) vs one lh_join_aggregate per
+    query, with the autotuned thresholds."""
+    import torch
+    from paper_1708_07859_b300 import inputs as gen
+    ns, ms = gen.batch_graph_sizes(count)
+    graphs = [(i % 2, gen.batch_graph(i, ns[i], ms[i])) for i in range(count)]
+    tries, queries, joins = [], [], []
+    for kind, (s, d) in graphs:
+        ds, dd = lh.to_device_u32(s), lh.to_device_u32(d)
+        t = ctx.build_trie([ds, dd], key_order=[0, 1])
+        tries.append(t)
+        queries.append((kind, t))
+        joins.append(lh.GraphJoin(ctx, ds, dd, "triangle" if kind == 0 else "clique4"))
+    tuning, tune_ms = lh.batch_autotune(ctx, queries)
+    b = lh.Batch(ctx, queries, tuning)
+    b.run()
+    counts = b.result()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    reps = 5
+    for _ in range(reps):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    plans = [lh.make_plan(list(range(j.n_attrs))) for j in joins]
+    seq = []
+    for j, p in zip(joins, plans):       # warm the per-query tries
+        seq.append(j.run(p)[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j, p in zip(joins, plans):
+        j.run(p)
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3
+    same = bool(np.array_equal(np.asarray(seq, dtype=np.uint64), counts))
+    edges = int(sum(int(s.size) for _, (s, _) in graphs))
+    b.free()
+    for t in tries:
+        t.free()
+    for j in joins:
+        j.free()
+    return {"queries": count, "edges": edges, "tuning": {"t_warp": tuning[0], "chunk": tuning[1],
+                                                        "ctas_per_sm": tuning[2]},
+            "batch_ms": batch_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batch_ms,
+            "identical_counts": same, "edges_per_s_batch": edges / (batch_ms / 1e3)}
+
+
 # ------------------------------------------------------------- CPU baseline
 
 def cpu_baseline(A, B, x, n_rows, target_s=15.0):
@@ -374,6 +447,14 @@ def main():
         dist_init("nccl")
     dev_id = torch.cuda.current_device()
     from paper_1708_07859_b300 import lh
+    if args.isect_only or args.extras_only:
+        ctx = lh.Context()
+        if args.isect_only:
+            print(json.dumps({"intersect_fig4a": intersect_fig4a(ctx, lh, load_peaks()[0])}))
+        else:
+            print(json.dumps({"planner": planner_compare(ctx, lh), "batched": batched_compare(ctx, lh)}))
+        ctx.close()
+        return 0
 
     A, B, x, Dm, Dn = make_inputs(args.rows, rank)
     elems, union = step_elements(A, B)
@@ -482,6 +563,10 @@ def main():
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_total / args.steps}
 
     fig4a = None if args.no_isect else intersect_fig4a(ctx, lh, hbm_peak)
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["planner"] = planner_compare(ctx, lh)
+        extras["batched"] = batched_compare(ctx, lh)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -499,7 +584,7 @@ def main():
                            "l2": "256 MB buffer written between timed steps; inputs 400 MB > L2",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "kernel_ms_per_step": breakdown, "intersect_fig4a": fig4a}
+                "clocks": clocks, "kernel_ms_per_step": breakdown, "intersect_fig4a": fig4a, **extras}
         print(json.dumps(line))
     ctx.close()
     if world > 1:

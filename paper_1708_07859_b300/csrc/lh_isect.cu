@@ -271,7 +271,10 @@ struct __align__(16) TileDesc {
     uint32_t la, lb;     // merge: slice lengths; probe / ubs: elements; bs: words
     uint32_t pair, kind; // kind | 256 when the merge slice of B has one extra head element
     uint64_t bn;         // probe: |B|; ubs: B words
-    uint32_t bbase, pad; // ubs: B base value
+    uint32_t bbase;      // ubs: B base value
+    uint32_t room;       // merge: elements after each slice that stay inside
+                         // its array (A: bits 0-1, B: bits 2-3, at most 3);
+                         // bit 4: both arrays 16-byte aligned
 };
 
 __global__ void k_isect_tiles(uint32_t npairs, const lh_set *A, const lh_set *B, const PairPlan *plan,
@@ -289,7 +292,7 @@ __global__ void k_isect_tiles(uint32_t npairs, const lh_set *A, const lh_set *B,
         d.kind = pl.kind;
         d.bn = 0;
         d.bbase = 0;
-        d.pad = 0;
+        d.room = 0;
         if (pl.kind == K_MERGE) {
             const uint64_t nd = a.n + b.n;
             const uint64_t d0 = t * kTile, d1 = min(nd, d0 + kTile);
@@ -301,6 +304,9 @@ __global__ void k_isect_tiles(uint32_t npairs, const lh_set *A, const lh_set *B,
             d.la = (uint32_t)(i1 - i0);
             d.lb = (uint32_t)(j1 - j0);
             if (j1 < b.n) d.kind |= 256u;
+            const uint64_t bend = j1 + (j1 < b.n ? 1 : 0);
+            d.room = (uint32_t)min((uint64_t)3, a.n - i1) | ((uint32_t)min((uint64_t)3, b.n - bend) << 2);
+            if (((uintptr_t)a.data & 15u) == 0 && ((uintptr_t)b.data & 15u) == 0) d.room |= 16u;
         } else if (pl.kind == K_BB) {
             const uint64_t w0 = pl.lo_w + t * kTile, w1 = min(pl.hi_w, w0 + kTile);
             d.a = a.data + (w0 - (a.base >> 5));
@@ -431,6 +437,211 @@ __global__ void __launch_bounds__(kThreads) k_isect2(const TileDesc *desc, uint6
     }
 }
 
+// ---- TMA-staged merge tiles ------------------------------------------------
+// Merge slices are staged by cp.async.bulk (one copy per slice, issued by one
+// thread, completion on an mbarrier) into two shared buffers: the next tile's
+// slices load while the current one is merged.  A copy must start and end on
+// 16-byte boundaries, so it covers the slice rounded out to whole 16-byte
+// words where the array allows it; elements the rounded copy cannot cover
+// (a slice end closer than 16 bytes to its array's end) are fetched with
+// plain loads.  Descriptors are read two tiles ahead.  Waits are bounded.
+
+constexpr uint32_t kBufA = kTile + 8, kBufB = kTile + 16;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init1(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Copy window of a slice [p, p + len) whose array has `room` readable
+// elements after the slice: the 16-byte words from the one holding p up to
+// the end rounded up (or down, when rounding up would leave the array), as
+// element offsets [lo, hi) relative to p (lo in -3..0; no window when hi <= lo
+// or the arrays are not 16-byte aligned).
+__device__ __forceinline__ void copy_window(const uint32_t *p, uint32_t len, uint32_t room, bool aligned, int &lo,
+                                            int &hi) {
+    lo = hi = 0;
+    if (!aligned) return;
+    const int64_t a = (int64_t)(((uintptr_t)p) >> 2);
+    const int64_t start = a & ~3ll, end = a + len;
+    const int64_t up = (end + 3) & ~3ll;
+    const int64_t stop = (up - end <= (int64_t)room) ? up : (end & ~3ll);
+    lo = (int)(start - a);
+    hi = (int)(stop - a);
+    if (hi < lo) hi = lo;
+}
+
+// Issue the staging of merge tile d into buffers (sa, sb): thread 0 arms the
+// barrier and starts the bulk copies; every thread plain-loads its share of
+// the elements the copies leave out.  Returns the buffer offsets of element 0.
+__device__ __forceinline__ void stage_merge(const TileDesc &d, uint32_t *sa, uint32_t *sb, uint64_t *bar, int &offa,
+                                            int &offb) {
+    const bool aligned = (d.room >> 4) & 1u;
+    const uint32_t lbx = d.lb + ((d.kind >> 8) & 1u);
+    int alo, ahi, blo, bhi;
+    copy_window(d.a, d.la, d.room & 3u, aligned, alo, ahi);
+    copy_window(d.b, lbx, (d.room >> 2) & 3u, aligned, blo, bhi);
+    offa = -alo;
+    offb = -blo;
+    const uint32_t na = (uint32_t)(ahi - alo), nb = (uint32_t)(bhi - blo);
+    if (threadIdx.x == 0) {
+        // earlier generic-proxy reads of this buffer come before the async copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arm(bar, 4u * (na + nb));
+        if (na) bulk_g2s(sa, d.a + alo, 4u * na, bar);
+        if (nb) bulk_g2s(sb, d.b + blo, 4u * nb, bar);
+    }
+    // elements past the copy windows
+    const uint32_t a_from = na ? (uint32_t)max(ahi, 0) : 0u, b_from = nb ? (uint32_t)max(bhi, 0) : 0u;
+    for (uint32_t k = a_from + threadIdx.x; k < d.la; k += kThreads) sa[offa + k] = __ldg(d.a + k);
+    for (uint32_t k = b_from + threadIdx.x; k < lbx; k += kThreads) sb[offb + k] = __ldg(d.b + k);
+}
+
+__global__ void __launch_bounds__(kThreads) k_isect3(const TileDesc *desc, uint64_t total, uint64_t *counts,
+                                                     uint32_t *status) {
+    __shared__ __align__(128) uint32_t sa[2][kBufA];
+    __shared__ __align__(128) uint32_t sb[2][kBufB];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t red[kThreads / 32];
+    uint64_t tile = blockIdx.x;
+    if (tile >= total) return;
+    if (threadIdx.x == 0) {
+        mbar_init1(&bar[0]);
+        mbar_init1(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // merge tiles staged into each buffer so far, and the staged offsets
+    // (block-uniform values)
+    uint32_t uses0 = 0, uses1 = 0;
+    int offa0 = 0, offb0 = 0, offa1 = 0, offb1 = 0;
+    TileDesc d = desc[tile];
+    const uint64_t t1 = tile + gridDim.x;
+    TileDesc dn = d;
+    if (t1 < total) dn = desc[t1];
+    uint32_t buf = 0;
+    if ((d.kind & 255u) == K_MERGE) {
+        stage_merge(d, sa[0], sb[0], &bar[0], offa0, offb0);
+        uses0++;
+    }
+    while (tile < total) {
+        const uint64_t next = tile + gridDim.x;
+        const uint64_t next2 = next + gridDim.x;
+        TileDesc dnn = dn;
+        if (next2 < total) dnn = desc[next2];
+        const bool stage_next = next < total && (dn.kind & 255u) == K_MERGE;
+        // the next merge tile goes into the other buffer (free since the last barrier)
+        if (stage_next) {
+            if (buf == 0) { stage_merge(dn, sa[1], sb[1], &bar[1], offa1, offb1); uses1++; }
+            else { stage_merge(dn, sa[0], sb[0], &bar[0], offa0, offb0); uses0++; }
+        }
+        const uint32_t kind = d.kind & 255u;
+        const bool has_ext = (d.kind >> 8) & 1u;
+        const uint32_t la = d.la, lb = d.lb;
+        bool waited = true;
+        if (kind == K_MERGE) waited = mbar_wait_bounded(&bar[buf], ((buf ? uses1 : uses0) - 1) & 1u);
+        if (__syncthreads_or(!waited)) {
+            // a copy never landed: record it, let the other buffer's copy (if
+            // one was issued) land, and stop
+            if (threadIdx.x == 0) lh_set_status(status, LH_ETIMEOUT);
+            if (stage_next) mbar_wait_bounded(&bar[buf ^ 1], ((buf ? uses0 : uses1) - 1) & 1u);
+            __syncthreads();
+            break;
+        }
+        uint32_t cnt = 0;
+        const uint32_t *A = sa[buf] + (buf ? offa1 : offa0), *Bv = sb[buf] + (buf ? offb1 : offb0);
+        if (kind == K_MERGE) {
+            const uint32_t s = threadIdx.x * kItems;
+            const uint32_t e = min(s + kItems, la + lb);
+            if (s < e) {
+                uint32_t ii = sm_split(A, la, Bv, lb, s);
+                uint32_t jj = s - ii;
+                for (uint32_t step = s; step < e; ++step) {
+                    if (ii < la && (jj >= lb || A[ii] <= Bv[jj])) {
+                        const uint32_t av = A[ii];
+                        const bool head = jj < lb || (jj == lb && has_ext);
+                        if (head && Bv[jj] == av) ++cnt;
+                        ++ii;
+                    } else {
+                        ++jj;
+                    }
+                }
+            }
+        } else if (kind == K_UBS || kind == K_PROBE) {
+            uint32_t x[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                x[r] = k < la ? __ldg(d.a + k) : 0u;
+            }
+            if (kind == K_UBS) {
+                uint32_t w[kItems];
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) {
+                    const uint32_t k = threadIdx.x + r * kThreads;
+                    const uint32_t dd = x[r] - d.bbase;
+                    const bool in = k < la && x[r] >= d.bbase && (uint64_t)(dd >> 5) < d.bn;
+                    w[r] = in ? __ldg(d.b + (dd >> 5)) : 0u;
+                }
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((x[r] - d.bbase) & 31u)) & 1u;
+            } else {
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) {
+                    const uint32_t k = threadIdx.x + r * kThreads;
+                    if (k >= la) continue;
+                    uint64_t l = 0, h = d.bn;
+                    while (l < h) {
+                        const uint64_t m = (l + h) >> 1;
+                        if (__ldg(d.b + m) < x[r]) l = m + 1;
+                        else h = m;
+                    }
+                    cnt += (l < d.bn && __ldg(d.b + l) == x[r]) ? 1u : 0u;
+                }
+            }
+        } else if (kind == K_BB) {
+            const uint4 *pa = (const uint4 *)d.a;
+            const uint4 *pb = (const uint4 *)d.b;
+            const uint32_t nv = la >> 2;
+            for (uint32_t k = threadIdx.x; k < nv; k += kThreads) {
+                const uint4 xx = __ldg(pa + k), yy = __ldg(pb + k);
+                cnt += __popc(xx.x & yy.x) + __popc(xx.y & yy.y) + __popc(xx.z & yy.z) + __popc(xx.w & yy.w);
+            }
+        }
+        const uint32_t tot = block_sum(cnt, red);  // ends with a barrier: this buffer is free again
+        if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + d.pair), (unsigned long long)tot);
+        // the next tile, if it is a merge tile, sits in the other buffer
+        if (stage_next) buf ^= 1;
+        tile = next;
+        d = dn;
+        dn = dnn;
+    }
+}
+
 }  // namespace
 
 extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
@@ -456,10 +667,10 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
         LH_TRACED(ctx, "k_isect_tiles", k_isect_tiles<<<lh_blocks(ntiles, 256, (unsigned)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
                                             npairs, a, b, plan, off, desc));
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect2, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect3, kThreads, 0);
         if (per_sm < 1) per_sm = 1;
         unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * per_sm);
-        LH_TRACED(ctx, "k_isect", k_isect2<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts));
+        LH_TRACED(ctx, "k_isect", k_isect3<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts, ctx->d_status));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "intersect: %s", cudaGetErrorString(e));
     }

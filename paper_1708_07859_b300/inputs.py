@@ -133,11 +133,14 @@ def triangle_workload(seed_offset: int = 1, n: int = 4096, m: int = 32768):
 
 def batch_graph_sizes(count: int = 4096, seed_offset: int = 4):
     """Edge counts m_i = round(exp(U[ln 100, ln 1e5])) and vertex counts
-    n_i = max(16, ceil(m_i / 8)) for a batch of independent graphs."""
+    n_i = max(16, ceil(m_i / 8), smallest n with C(n, 2) >= m_i) for a batch
+    of independent graphs."""
     rng = _rng(SEED_BASE + seed_offset)
     m = np.rint(np.exp(rng.uniform(math.log(100.0), math.log(1e5), size=count))).astype(np.int64)
     n = np.maximum(16, np.ceil(m / 8.0)).astype(np.int64)
-    return n, m
+    # at least enough vertices for m distinct pairs: C(n, 2) >= m
+    n_min = np.ceil((1.0 + np.sqrt(1.0 + 8.0 * m)) / 2.0).astype(np.int64)
+    return np.maximum(n, n_min), m
 
 
 def batch_graph(i: int, n: int, m: int, seed_offset: int = 4):

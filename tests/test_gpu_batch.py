@@ -32,7 +32,7 @@ def test_batch_vs_oracle_and_replay(ctx, orc, lhlib):
     graphs = []
     for i in range(48):
         m = int(min(ms[i], 20000))
-        n = int(max(16, math.ceil(m / 8)))
+        n = int(max(16, math.ceil(m / 8), math.ceil((1 + math.sqrt(1 + 8 * m)) / 2)))
         graphs.append((i % 2, gen.batch_graph(i, n, m)))
     graphs.append((0, gen.complete_graph(30)))
     graphs.append((1, gen.complete_graph(30)))
