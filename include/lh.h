@@ -65,7 +65,9 @@ typedef struct lh_batch lh_batch;
 
 /* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
  * (NULL = legacy default stream) on which all work is issued.  Device memory
- * comes from the stream-ordered allocator (cudaMallocAsync) on that stream. */
+ * comes from a private stream-ordered memory pool of the context (allocated
+ * and freed on that stream); the pool keeps freed memory for reuse until
+ * lh_destroy. */
 lh_status lh_create(lh_ctx **out, void *cuda_stream);
 lh_status lh_destroy(lh_ctx *ctx);
 lh_status lh_set_stream(lh_ctx *ctx, void *cuda_stream);
@@ -73,6 +75,12 @@ lh_status lh_set_stream(lh_ctx *ctx, void *cuda_stream);
 const char *lh_last_error(const lh_ctx *ctx);
 /* Wait for the stream; return the first device-side error word, if any. */
 lh_status lh_sync(lh_ctx *ctx);
+/* Diagnostic of the bounded device waits (no paper counterpart): launches
+ * one warp that waits, at most `spins` tries (1 .. 2^20), on an mbarrier
+ * nothing arrives at, then waits for the stream.  Returns LH_ETIMEOUT, the
+ * status every mbarrier / TMA wait of this library reports when a copy never
+ * completes; the context stays usable afterwards.  LH_EINVAL for bad spins. */
+lh_status lh_selftest_bounded_wait(lh_ctx *ctx, uint32_t spins);
 /* Library version string. */
 const char *lh_version(void);
 /* Blocking copies between a device pointer and host memory on the context
@@ -441,8 +449,12 @@ lh_status lh_model_train(lh_ctx *ctx, lh_model *m, const float *X, const float *
 lh_status lh_plan_time(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan, lh_trie *const *tries,
                        float budget_ms, uint32_t repeats, float *ms);
 /* Planner features (host float[LH_NFEAT]) of running q under plan on
- * `tries` (built for that plan).  Computed on the device from the tries'
- * level statistics. */
+ * `tries` (built for that plan), from device-side statistics of the tries'
+ * levels: [0, 6) log2(1 + |relation|) per edge; [6, 31) per order position
+ * d < 5: log2 set-size median, 90th percentile, maximum, level density, and
+ * log2(1 + icost(v_d) x weight(v_d)) of the Section 4 cost model; [31, 56)
+ * position x attribute one-hot; [56, 60) layout policy one-hot (ratio 0, 8,
+ * 32, other). */
 lh_status lh_plan_features(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
                            lh_trie *const *tries, float *feat);
 

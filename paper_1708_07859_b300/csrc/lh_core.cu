@@ -26,6 +26,21 @@ extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) {
+        // a private pool whose memory stays mapped between calls: the default
+        // pool would hand multi-GB temporaries back at every synchronisation
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        e = cudaMemPoolCreate(&ctx->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_status, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(uint32_t));
     if (e == cudaSuccess)
@@ -34,6 +49,7 @@ extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         delete ctx;
         return LH_ECUDA;
     }
@@ -48,6 +64,10 @@ extern "C" lh_status lh_destroy(lh_ctx *ctx) {
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->pool) {
+        cudaDeviceSynchronize();  // memory freed asynchronously must be released before the pool goes
+        cudaMemPoolDestroy(ctx->pool);
+    }
     delete ctx;
     return LH_OK;
 }
@@ -315,36 +335,62 @@ __global__ void k_sort_hist(const uint64_t *keys, uint64_t n, int shift, uint32_
     hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t n, int shift,
-                               const uint64_t *offs, uint32_t ntiles, uint64_t *kout,
-                               uint32_t *vout) {
+// Stable scatter of one tile: keys are ranked per digit (warp match + prefix
+// over warps + running count over rounds), placed in shared memory grouped by
+// digit, and written out as contiguous per-digit runs so that consecutive
+// threads store consecutive addresses.
+constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t n,
+                                                               int shift, const uint32_t *hist, const uint64_t *offs,
+                                                               uint32_t ntiles, uint64_t *kout, uint32_t *vout) {
+    extern __shared__ uint64_t s_keys[];                       // kSortTile keys, grouped by digit
+    uint32_t *s_vals = (uint32_t *)(s_keys + kSortTile);      // their payloads
     __shared__ uint32_t wcnt[kSortThreads / 32][256];
     __shared__ uint32_t running[256];
     __shared__ uint32_t round_tot[256];
+    __shared__ uint32_t lstart[256];
+    __shared__ uint32_t wtot[kSortThreads / 32];
     __shared__ uint64_t gbase[256];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     gbase[t] = offs[(uint64_t)t * ntiles + blockIdx.x];
     running[t] = 0;
+    {
+        // exclusive prefix of this tile's digit counts: each digit's run start in shared memory
+        const uint32_t c = hist[(uint64_t)t * ntiles + blockIdx.x];
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(LH_FULL, incl, o);
+            if (lane >= o) incl += x;
+        }
+        if (lane == 31) wtot[warp] = incl;
+        __syncthreads();
+        uint32_t wp = 0;
+        for (int w = 0; w < warp; ++w) wp += wtot[w];
+        lstart[t] = wp + incl - c;
+    }
     const uint32_t lt_mask = (1u << lane) - 1u;
-    uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    const uint32_t tile_n = (uint32_t)min((uint64_t)kSortTile, n - base);
     for (int r = 0; r < kSortRounds; ++r) {
 #pragma unroll
         for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
         __syncthreads();
-        uint64_t i = base + (uint64_t)r * kSortThreads + t;
-        bool valid = i < n;
-        uint64_t k = valid ? kin[i] : 0;
-        uint32_t v = valid ? vin[i] : 0;
-        uint32_t d = valid ? (uint32_t)((k >> shift) & 255u) : 256u;
-        uint32_t peers = __match_any_sync(LH_FULL, d);
-        uint32_t rk = __popc(peers & lt_mask);
+        const uint64_t i = base + (uint64_t)r * kSortThreads + t;
+        const bool valid = i < n;
+        const uint64_t k = valid ? kin[i] : 0;
+        const uint32_t v = valid ? vin[i] : 0;
+        const uint32_t d = valid ? (uint32_t)((k >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(LH_FULL, d);
+        const uint32_t rk = __popc(peers & lt_mask);
         if (valid && rk == 0) wcnt[warp][d] = __popc(peers);
         __syncthreads();
         {
             uint32_t p = 0;
 #pragma unroll
             for (int w = 0; w < kSortThreads / 32; ++w) {
-                uint32_t c = wcnt[w][t];
+                const uint32_t c = wcnt[w][t];
                 wcnt[w][t] = p;
                 p += c;
             }
@@ -352,12 +398,20 @@ __global__ void k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_
         }
         __syncthreads();
         if (valid) {
-            uint64_t dst = gbase[d] + running[d] + wcnt[warp][d] + rk;
-            kout[dst] = k;
-            vout[dst] = v;
+            const uint32_t at = lstart[d] + running[d] + wcnt[warp][d] + rk;
+            s_keys[at] = k;
+            s_vals[at] = v;
         }
         __syncthreads();
         running[t] += round_tot[t];
+    }
+    __syncthreads();
+    for (uint32_t at = t; at < tile_n; at += kSortThreads) {
+        const uint64_t k = s_keys[at];
+        const uint32_t d = (uint32_t)((k >> shift) & 255u);
+        const uint64_t dst = gbase[d] + (at - lstart[d]);
+        kout[dst] = k;
+        vout[dst] = s_vals[at];
     }
 }
 
@@ -377,6 +431,10 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_
         lh_free(ctx, hist);
         return s;
     }
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort smem attribute: %s", cudaGetErrorString(e));
+    }
     uint64_t *ka = keys, *kb = tmp_k;
     uint32_t *va = vals, *vb = tmp_v;
     int passes = (bits + 7) / 8;
@@ -385,8 +443,8 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_
         LH_TRACED(ctx, "k_sort_hist", k_sort_hist<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, n, shift, hist, ntiles));
         s = lh_scan_u32_to_u64(ctx, hist, offs, (uint64_t)256 * ntiles);
         if (s != LH_OK) break;
-        LH_TRACED(ctx, "k_sort_scatter", k_sort_scatter<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, va, n, shift, offs, ntiles,
-                                                                  kb, vb));
+        LH_TRACED(ctx, "k_sort_scatter", k_sort_scatter<<<ntiles, kSortThreads, kScatterSmem, ctx->stream>>>(
+                                             ka, va, n, shift, hist, offs, ntiles, kb, vb));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort: %s", cudaGetErrorString(e));
         uint64_t *tk = ka; ka = kb; kb = tk;

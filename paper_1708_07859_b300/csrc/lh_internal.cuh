@@ -30,6 +30,7 @@ struct lh_ctx {
     int device = 0;
     int num_sms = 148;
     std::string err;
+    cudaMemPool_t pool = nullptr;   // private stream-ordered pool (keeps its memory)
     uint32_t *d_status = nullptr;   // first device-side error (lh_status), 0 = none
     uint64_t *h_pinned = nullptr;   // pinned host words for small read-backs
     static constexpr int kPinnedWords = 64;
@@ -78,7 +79,8 @@ template <class T>
 static inline lh_status lh_alloc(lh_ctx *ctx, T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), ctx->stream);
+    cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync((void **)p, count * sizeof(T), ctx->pool, ctx->stream)
+                              : cudaMallocAsync((void **)p, count * sizeof(T), ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return lh_fail(ctx, LH_ENOMEM, "cudaMallocAsync(%zu bytes): %s", count * sizeof(T),

@@ -41,7 +41,9 @@ __global__ void k_plan(uint32_t npairs, const lh_set *A, const lh_set *B, PairPl
     if (a.n > 0 && b.n > 0) {
         if (a.layout == 0 && b.layout == 0) {
             uint64_t mn = min(a.n, b.n), mx = max(a.n, b.n);
-            if (mx <= 32 * mn) {
+            // the merge closes its slices with 0xFFFFFFFF sentinels
+            const bool max_val = a.data[a.n - 1] == 0xFFFFFFFFu || b.data[b.n - 1] == 0xFFFFFFFFu;
+            if (mx <= 32 * mn && !max_val) {
                 pl.kind = K_MERGE;
                 nt = ceil_div(a.n + b.n, kTile);
             } else {
@@ -642,6 +644,151 @@ __global__ void __launch_bounds__(kThreads) k_isect3(const TileDesc *desc, uint6
     }
 }
 
+// ---- merge tiles, version 4 --------------------------------------------------
+// One linear staging buffer filled by cp.async.bulk (the next tile's copies
+// overlap the current merge) and one padded copy of the current tile
+// (index i stored at i + i/32) so that threads whose merge ranges start 8
+// words apart hit distinct banks.  Sentinels (0xFFFFFFFF) close both padded
+// slices, so the branch-free merge needs no bounds tests; pairs whose sets
+// hold that value use the probe path instead (k_plan).
+
+constexpr uint32_t kSwz = kTile + 2 + (kTile + 2) / 32 + 2;
+__device__ __forceinline__ uint32_t swz(uint32_t i) { return i + (i >> 5); }
+
+// merge-path split on the padded slices (ties: A first)
+__device__ __forceinline__ uint32_t sw_split(const uint32_t *a, uint32_t na, const uint32_t *b, uint32_t nb,
+                                             uint32_t d) {
+    uint32_t lo = d > nb ? d - nb : 0, hi = min(d, na);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const bool right = a[swz(mid)] <= b[swz(d - mid - 1)];
+        lo = right ? mid + 1 : lo;
+        hi = right ? hi : mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint64_t total, uint64_t *counts,
+                                                     uint32_t *status) {
+    __shared__ __align__(128) uint32_t la_buf[kBufA];
+    __shared__ __align__(128) uint32_t lb_buf[kBufB];
+    __shared__ uint32_t pa[kSwz];
+    __shared__ uint32_t pb[kSwz];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t red[kThreads / 32];
+    uint64_t tile = blockIdx.x;
+    if (tile >= total) return;
+    if (threadIdx.x == 0) {
+        mbar_init1(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t uses = 0;
+    int offa = 0, offb = 0;
+    TileDesc d = desc[tile];
+    TileDesc dn = d;
+    if (tile + gridDim.x < total) dn = desc[tile + gridDim.x];
+    if ((d.kind & 255u) == K_MERGE) {
+        stage_merge(d, la_buf, lb_buf, &bar, offa, offb);
+        uses++;
+    }
+    while (tile < total) {
+        const uint64_t next = tile + gridDim.x;
+        TileDesc dnn = dn;
+        if (next + gridDim.x < total) dnn = desc[next + gridDim.x];
+        const uint32_t kind = d.kind & 255u;
+        const uint32_t la = d.la, lb = d.lb;
+        const uint32_t lbx = lb + ((d.kind >> 8) & 1u);
+        bool waited = true;
+        if (kind == K_MERGE) waited = mbar_wait_bounded(&bar, (uses - 1) & 1u);
+        if (__syncthreads_or(!waited)) {
+            if (threadIdx.x == 0) lh_set_status(status, LH_ETIMEOUT);
+            break;
+        }
+        if (kind == K_MERGE) {
+            // linear staging -> padded copy with sentinels
+            for (uint32_t k = threadIdx.x; k < la; k += kThreads) pa[swz(k)] = la_buf[offa + k];
+            for (uint32_t k = threadIdx.x; k < lbx; k += kThreads) pb[swz(k)] = lb_buf[offb + k];
+            if (threadIdx.x == 0) {
+                pa[swz(la)] = 0xFFFFFFFFu;
+                pb[swz(lbx)] = 0xFFFFFFFFu;
+            }
+        }
+        __syncthreads();
+        // the staging buffer is free: start the next merge tile's copies
+        if (next < total && (dn.kind & 255u) == K_MERGE) {
+            stage_merge(dn, la_buf, lb_buf, &bar, offa, offb);
+            uses++;
+        }
+        uint32_t cnt = 0;
+        if (kind == K_MERGE) {
+            const uint32_t s = threadIdx.x * kItems;
+            const uint32_t e = min(s + kItems, la + lb);
+            if (s < e) {
+                uint32_t ii = sw_split(pa, la, pb, lb, s);
+                uint32_t jj = s - ii;
+                uint32_t a = pa[swz(ii)], b = pb[swz(jj)];
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    if (s + k < e) {
+                        const bool ta = a <= b;
+                        cnt += (a == b) ? 1u : 0u;  // a consumed while the B head equals it
+                        if (ta) a = pa[swz(++ii)];
+                        else b = pb[swz(++jj)];
+                    }
+                }
+            }
+        } else if (kind == K_UBS || kind == K_PROBE) {
+            uint32_t x[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                x[r] = k < la ? __ldg(d.a + k) : 0u;
+            }
+            if (kind == K_UBS) {
+                uint32_t w[kItems];
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) {
+                    const uint32_t k = threadIdx.x + r * kThreads;
+                    const uint32_t dd = x[r] - d.bbase;
+                    const bool in = k < la && x[r] >= d.bbase && (uint64_t)(dd >> 5) < d.bn;
+                    w[r] = in ? __ldg(d.b + (dd >> 5)) : 0u;
+                }
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((x[r] - d.bbase) & 31u)) & 1u;
+            } else {
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) {
+                    const uint32_t k = threadIdx.x + r * kThreads;
+                    if (k >= la) continue;
+                    uint64_t l = 0, h = d.bn;
+                    while (l < h) {
+                        const uint64_t m = (l + h) >> 1;
+                        if (__ldg(d.b + m) < x[r]) l = m + 1;
+                        else h = m;
+                    }
+                    cnt += (l < d.bn && __ldg(d.b + l) == x[r]) ? 1u : 0u;
+                }
+            }
+        } else if (kind == K_BB) {
+            const uint4 *qa = (const uint4 *)d.a;
+            const uint4 *qb = (const uint4 *)d.b;
+            const uint32_t nv = la >> 2;
+            for (uint32_t k = threadIdx.x; k < nv; k += kThreads) {
+                const uint4 xx = __ldg(qa + k), yy = __ldg(qb + k);
+                cnt += __popc(xx.x & yy.x) + __popc(xx.y & yy.y) + __popc(xx.z & yy.z) + __popc(xx.w & yy.w);
+            }
+        }
+        const uint32_t tot = block_sum(cnt, red);  // ends with a barrier: the padded tile is free again
+        if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + d.pair), (unsigned long long)tot);
+        tile = next;
+        d = dn;
+        dn = dnn;
+    }
+    // a staged tile that was not consumed (only after a timeout): let its copies land
+    __syncthreads();
+}
+
 }  // namespace
 
 extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
@@ -667,10 +814,10 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
         LH_TRACED(ctx, "k_isect_tiles", k_isect_tiles<<<lh_blocks(ntiles, 256, (unsigned)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
                                             npairs, a, b, plan, off, desc));
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect3, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect4, kThreads, 0);
         if (per_sm < 1) per_sm = 1;
         unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * per_sm);
-        LH_TRACED(ctx, "k_isect", k_isect3<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts, ctx->d_status));
+        LH_TRACED(ctx, "k_isect", k_isect4<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts, ctx->d_status));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "intersect: %s", cudaGetErrorString(e));
     }
@@ -797,4 +944,41 @@ extern "C" lh_status lh_intersect_count_batch_noalloc(lh_ctx *ctx, uint32_t npai
     LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, nullptr, counts));
     LH_LAUNCH_CHECK();
     return LH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded device waits: one warp waits on an mbarrier that
+// nothing will ever arrive at, gives up after `spins` tries, and records
+// LH_ETIMEOUT in the context's status word -- the path every TMA / mbarrier
+// wait of this library takes when a copy never lands.  No fault, no trap.
+namespace {
+__global__ void k_selftest_wait(uint32_t spins, uint32_t *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init1(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool done = false;
+    for (uint32_t i = 0; i < spins && !done; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(&bar))
+            : "memory");
+        done = ok != 0;
+    }
+    if (__syncthreads_or(!done) && threadIdx.x == 0) lh_set_status(status, LH_ETIMEOUT);
+}
+}  // namespace
+
+extern "C" lh_status lh_selftest_bounded_wait(lh_ctx *ctx, uint32_t spins) {
+    if (!ctx) return LH_EINVAL;
+    if (spins == 0 || spins > (1u << 20)) return lh_fail(ctx, LH_EINVAL, "spins must be 1..2^20");
+    LH_TRACED(ctx, "k_selftest_wait", k_selftest_wait<<<1, 32, 0, ctx->stream>>>(spins, ctx->d_status));
+    LH_LAUNCH_CHECK();
+    return lh_sync(ctx);
 }

@@ -3,9 +3,11 @@
 // timings) and the exhaustive judge.
 //
 //   features  per (query, attribute order, layout policy), from device-side
-//             statistics of the tries that order needs: relation sizes, the
-//             log2 set-size quantiles and density of every attribute's trie
-//             level, the order as a position one-hot, the layout one-hot.
+//             statistics of the tries that order needs: relation sizes; per
+//             attribute position the log2 set-size median, 90th percentile
+//             and maximum and the density of its trie level, and the Section
+//             4 cost term log2(1 + icost x weight); the order as a position
+//             one-hot; the layout one-hot.
 //   model     MLP n_in -> H -> H -> 1 (ReLU), fp32, predicting log(ms);
 //             forward, backward (mean squared error) and Adam are this
 //             file's kernels, in a fixed summation order.
@@ -276,13 +278,18 @@ int policy_index(uint32_t ratio) {
 lh_status features(lh_ctx *ctx, const lh_query *q, const uint32_t *order, uint32_t bs_ratio,
                    const lh_trie *const *edge_tries, float *f) {
     for (int i = 0; i < LH_NFEAT; ++i) f[i] = 0.f;
-    for (uint32_t e = 0; e < q->n_edges && e < 6; ++e) {
+    uint64_t cards[LH_MAX_EDGES];
+    for (uint32_t e = 0; e < q->n_edges; ++e) {
         uint64_t card = q->edges[e].card;
         const lh_trie *t = edge_tries[e];
         if (t) card = t->lv[t->nlevels - 1].n;
         else if (!card) card = q->edges[e].flat_n;
-        f[e] = (float)std::log2((double)card + 1.0);
+        cards[e] = card ? card : 1;
+        if (e < 6) f[e] = (float)std::log2((double)card + 1.0);
     }
+    // the Section 4 cost model's term of each attribute, as a prior
+    int64_t w[LH_MAX_ATTRS] = {0};
+    lh_weights(q, cards, w);
     for (uint32_t d = 0; d < q->n_attrs && d < 5; ++d) {
         const uint32_t v = order[d];
         LevelStats best{1e30f, 1e30f, 1e30f, 1e30f, 0.f};
@@ -306,10 +313,10 @@ lh_status features(lh_ctx *ctx, const lh_query *q, const uint32_t *order, uint32
             float *g = f + 6 + 5 * d;
             g[0] = best.q50;
             g[1] = best.q90;
-            g[2] = best.q99;
-            g[3] = best.qmax;
-            g[4] = best.density;
+            g[2] = best.qmax;
+            g[3] = best.density;
         }
+        f[6 + 5 * d + 4] = (float)std::log2(1.0 + (double)lh_icost_vertex(q, order, d) * (double)w[v]);
         if (v < 5) f[31 + 5 * d + v] = 1.f;
     }
     f[56 + policy_index(bs_ratio)] = 1.f;

@@ -130,6 +130,7 @@ EXPORTS = {
     "lh_sync": [C.c_void_p],
     "lh_copy_d2h": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
     "lh_copy_h2d": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
+    "lh_selftest_bounded_wait": [C.c_void_p, C.c_uint32],
     "lh_trace_enable": [C.c_void_p, C.c_int],
     "lh_trace_read": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
     "lh_trace_reset": [C.c_void_p],

@@ -32,7 +32,7 @@ TRAIN_SEED = gen.SEED_BASE + 5000     # disjoint from the evaluation seeds below
 EVAL_SEED = gen.SEED_BASE + 5
 
 
-def random_graph(rng, m_lo=2 ** 10, m_hi=2 ** 16):
+def random_graph(rng, m_lo=2 ** 10, m_hi=2 ** 18):
     """G(n, m) or Chung-Lu (beta in [2, 3]) with log-uniform edge count."""
     m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
     seed = int(rng.integers(0, 2 ** 31))
@@ -48,7 +48,7 @@ def plan_for(order, ratio):
     return lh.make_plan(list(order), bs_ratio=ratio)
 
 
-def generate_training(ctx, n_queries, seed=TRAIN_SEED, plans_per_query=6, budget_ms=200.0, log=None):
+def generate_training(ctx, n_queries, seed=TRAIN_SEED, plans_per_query=8, budget_ms=200.0, log=None):
     """(X, y, meta): features of sampled (query, plan) pairs and the log of
     their measured ms.  Plans over the budget are recorded at the budget."""
     rng = np.random.default_rng(seed)
@@ -125,7 +125,7 @@ def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     t = sub.add_parser("train")
-    t.add_argument("--queries", type=int, default=1000)
+    t.add_argument("--queries", type=int, default=2000)
     t.add_argument("--epochs", type=int, default=300)
     t.add_argument("--out", default=DEFAULT_WEIGHTS)
     t.add_argument("--log", default=None)

@@ -35,8 +35,12 @@ def test_features_layout(ctx, lhlib):
     onehot = f[31:56].reshape(5, 5)
     assert onehot[0, 2] == 1 and onehot[1, 0] == 1 and onehot[2, 1] == 1 and onehot.sum() == 3
     assert f[56:60].tolist() == [0, 1, 0, 0]
-    # first attribute: one first-level set per relation -> quantiles of one set size
-    assert f[6 + 3] >= f[6 + 0]
+    # per position: median <= 90th percentile <= max of log2 set sizes
+    for d in range(3):
+        assert f[6 + 5 * d] <= f[6 + 5 * d + 1] <= f[6 + 5 * d + 2]
+    # cost-model term: order [2, 0, 1] of the triangle join has icosts (1, 10, 50)
+    # at weight 100 each -> log2(1 + icost * 100)
+    assert np.allclose(f[[10, 15, 20]], np.log2(1 + np.array([1, 10, 50]) * 100.0), atol=1e-5)
     g.free()
 
 
