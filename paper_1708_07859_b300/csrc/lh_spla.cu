@@ -289,10 +289,13 @@ struct EscSmem {
 // Bitonic network over 256 keys held 8 per lane at positions p = 8 * lane + e,
 // fully unrolled so every distance and direction test is a constant:
 // distances below 8 are register compare-exchanges, larger ones shuffles.
-template <class K>
+// FIRST: first merge stage (log2 of the run length it produces); runs of
+// length 2^(FIRST-1) must already be sorted, ascending for even run index
+// and descending for odd.
+template <class K, int FIRST = 1>
 __device__ __forceinline__ void esc_sort256(K (&key)[8], uint32_t lane) {
 #pragma unroll
-    for (int kk = 1; kk <= 8; ++kk) {
+    for (int kk = FIRST; kk <= 8; ++kk) {
         const uint32_t k = 1u << kk;
 #pragma unroll
         for (int jj = kk - 1; jj >= 0; --jj) {
@@ -365,27 +368,59 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
         S.ja[lane] = a;
         const uint32_t total = __shfl_sync(LH_FULL, incl, 31);
         __syncwarp();
-        // expand: products 8 * lane + e
+        // rows whose B rows all have one power-of-two length L (4..32) are
+        // 256-position bitonic inputs whose runs of L are already sorted: odd
+        // runs are laid out reversed and the network starts at runs of 2L
+        const uint32_t L0 = __shfl_sync(LH_FULL, blen, 0);
+        const bool has_q = q < ahi;
+        const bool uniform = __all_sync(LH_FULL, !has_q || blen == L0) && L0 >= 4 && L0 <= 32 &&
+                             (L0 & (L0 - 1)) == 0 && total <= kEscPairs;
         K key[8];
+        if (uniform) {
+            const uint32_t lg = 31 - __clz(L0);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const uint32_t t = (lane << 3) + e;
-            key[e] = ~K(0);
-            if (t < total) {
-                uint32_t lo = 0, hi = 31;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (S.jp[mid] > t) hi = mid;
-                    else lo = mid + 1;
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t t = (lane << 3) + e;
+                key[e] = ~K(0);
+                if (t < total) {
+                    const uint32_t r = t >> lg;
+                    uint32_t off = t & (L0 - 1);
+                    if (r & 1u) off = L0 - 1 - off;
+                    const uint32_t pos = S.jb[r] + off;
+                    float ph, pl;
+                    lh_two_prod(S.ja[r], __ldg(bv + pos), ph, pl);
+                    S.val[t] = make_float2(ph, pl);
+                    key[e] = ((K)__ldg(B.lv[1].vals + pos) << 8) | t;
                 }
-                const uint32_t pos = S.jb[lo] + (t - (S.jp[lo] - S.jl[lo]));
-                float ph, pl;
-                lh_two_prod(S.ja[lo], __ldg(bv + pos), ph, pl);
-                S.val[t] = make_float2(ph, pl);
-                key[e] = ((K)__ldg(B.lv[1].vals + pos) << 8) | t;
             }
+            switch (lg) {
+                case 2: esc_sort256<K, 3>(key, lane); break;
+                case 3: esc_sort256<K, 4>(key, lane); break;
+                case 4: esc_sort256<K, 5>(key, lane); break;
+                default: esc_sort256<K, 6>(key, lane); break;
+            }
+        } else {
+            // expand: products 8 * lane + e
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t t = (lane << 3) + e;
+                key[e] = ~K(0);
+                if (t < total) {
+                    uint32_t lo = 0, hi = 31;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (S.jp[mid] > t) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    const uint32_t pos = S.jb[lo] + (t - (S.jp[lo] - S.jl[lo]));
+                    float ph, pl;
+                    lh_two_prod(S.ja[lo], __ldg(bv + pos), ph, pl);
+                    S.val[t] = make_float2(ph, pl);
+                    key[e] = ((K)__ldg(B.lv[1].vals + pos) << 8) | t;
+                }
+            }
+            esc_sort256(key, lane);
         }
-        esc_sort256(key, lane);
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint32_t ps = esc_sk((lane << 3) + e);
