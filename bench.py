@@ -408,6 +408,31 @@ def batched_compare(ctx, lh, count=1024):
             "identical_counts": same, "edges_per_s_batch": edges / (batch_ms / 1e3)}
 
 
+def dram_traffic(kernel, rows):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel`
+    from the committed ncu capture (profiles/dram_traffic.json), scaled to
+    `rows` when the capture ran a smaller case; None when there is no capture
+    or the kernel's source file changed since it was taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1708_07859_b300", "csrc", rec["source"])
+    with open(src) as f:
+        text = f.read()
+    # the kernel's own source text: from its begin marker up to its end marker
+    a = text.find(rec["begin"])
+    b = text.find(rec["end"], a + 1)
+    if a < 0 or b < 0 or hashlib.sha256(text[a:b].encode()).hexdigest() != rec["source_sha256"]:
+        return None
+    return rec["bytes_per_launch"] * (rows / rec.get("rows", rows)) if rec.get("scales_with_rows") else \
+        rec["bytes_per_launch"]
+
+
 # ------------------------------------------------------------- CPU baseline
 
 def cpu_baseline(A, B, x, n_rows, target_s=15.0):
@@ -558,7 +583,7 @@ def main():
     else:
         achieved, peak, unit = None, hbm_peak, "GB/s"
     roof = {"kernel": name, "bound": bound or "hbm", "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": dram_traffic(name, args.rows),
             "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json' if peak_kind == 'measured' else 'profiling recipe fallback'})",
             "avg_launch_ms": avg_ms, "launches": n_launch,
             "algorithmic_bytes_per_launch" if bound != "tensor" else "algorithmic_flops_per_launch": alg}

@@ -373,14 +373,24 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *k
     const uint32_t lt_mask = (1u << lane) - 1u;
     const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
     const uint32_t tile_n = (uint32_t)min((uint64_t)kSortTile, n - base);
+    // all of this thread's keys are loaded up front: one memory latency per tile
+    uint64_t kr[kSortRounds];
+    uint32_t vr[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const uint64_t i = base + (uint64_t)r * kSortThreads + t;
+        kr[r] = i < n ? kin[i] : 0;
+        vr[r] = i < n ? vin[i] : 0;
+    }
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
 #pragma unroll
         for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
         __syncthreads();
         const uint64_t i = base + (uint64_t)r * kSortThreads + t;
         const bool valid = i < n;
-        const uint64_t k = valid ? kin[i] : 0;
-        const uint32_t v = valid ? vin[i] : 0;
+        const uint64_t k = kr[r];
+        const uint32_t v = vr[r];
         const uint32_t d = valid ? (uint32_t)((k >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(LH_FULL, d);
         const uint32_t rk = __popc(peers & lt_mask);

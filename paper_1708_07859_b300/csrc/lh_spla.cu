@@ -76,8 +76,12 @@ __global__ void k_spgemm_bound(DTrie A, DTrie B, uint32_t nA0, uint32_t *ub) {
     }
 }
 
-// Global hash capacity for rows above the shared bound (0 for the others).
-__global__ void k_spgemm_gcap(const uint32_t *ub, uint32_t n, uint64_t *gcap) {
+// Global hash capacity for rows above the shared bound (0 for the others),
+// and the number of rows the sort-based kernel does not take (more than
+// 256 products or more than 32 A entries).
+__global__ void k_spgemm_gcap(const uint32_t *ub, const uint32_t *aoffs, uint32_t n, uint64_t *gcap,
+                              unsigned long long *n_hash_rows) {
+    unsigned long long mine = 0;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         uint64_t u = ub[p];
         uint64_t c = 0;
@@ -86,7 +90,11 @@ __global__ void k_spgemm_gcap(const uint32_t *ub, uint32_t n, uint64_t *gcap) {
             while (c < 2 * u) c <<= 1;
         }
         gcap[p] = c;
+        mine += (u > kTab / 2 || aoffs[p + 1] - aoffs[p] > 32) ? 1ull : 0ull;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(LH_FULL, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(n_hash_rows, mine);
 }
 
 struct WarpSmem {
@@ -510,6 +518,8 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
     LH_TRY(res_alloc(ctx, r, &r->c_off, (size_t)n0 + 1));
     uint32_t *ub = nullptr, *cnt = nullptr, *gkey = nullptr, *tcol = nullptr;
     uint64_t *tmp_off = nullptr, *gcap = nullptr, *goff = nullptr;
+    unsigned long long *n_hash = nullptr;
+    unsigned long long hash_rows = 0;
     float *ghi = nullptr, *glo = nullptr, *tval = nullptr;
     lh_status s = LH_OK;
     uint64_t U = 0, G = 0, nnz = 0;
@@ -521,14 +531,17 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
     STEP(lh_alloc(ctx, &tmp_off, (size_t)n0 + 1));
     STEP(lh_alloc(ctx, &gcap, n0));
     STEP(lh_alloc(ctx, &goff, (size_t)n0 + 1));
+    STEP(lh_alloc(ctx, &n_hash, 1));
     if (s == LH_OK && n0) {
         LH_TRACED(ctx, "k_spgemm_bound", k_spgemm_bound<<<grid, T, 0, ctx->stream>>>(A, B, n0, ub));
-        LH_TRACED(ctx, "k_spgemm_gcap", k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(ub, n0, gcap));
+        cudaMemsetAsync(n_hash, 0, sizeof(unsigned long long), ctx->stream);
+        LH_TRACED(ctx, "k_spgemm_gcap", k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(ub, a->lv[0].offs, n0, gcap, n_hash));
     }
     STEP(lh_scan_u32_to_u64(ctx, ub, tmp_off, n0));
     STEP(lh_scan_u64_to_u64(ctx, gcap, goff, n0));
     STEP(lh_readback(ctx, tmp_off + n0, sizeof(uint64_t), &U));
     STEP(lh_readback(ctx, goff + n0, sizeof(uint64_t), &G));
+    STEP(lh_readback(ctx, n_hash, sizeof(unsigned long long), &hash_rows));
     STEP(lh_alloc(ctx, &tcol, U));
     STEP(lh_alloc(ctx, &tval, U));
     STEP(lh_alloc(ctx, &gkey, G));
@@ -551,7 +564,7 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         else
             LH_TRACED(ctx, "k_spgemm_esc", k_spgemm_esc<uint64_t><<<g3, kEscWarps * 32, 0, ctx->stream>>>(
                 A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ub, tmp_off, tcol, tval, cnt));
-        LH_TRACED(ctx, "k_spgemm_numeric", k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
+        if (hash_rows) LH_TRACED(ctx, "k_spgemm_numeric", k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
                                                                (const float *)b->anno[0], n0, tmp_off,
                                                                goff, gkey, ghi, glo, tcol, tval, cnt));
         cudaError_t e = cudaGetLastError();
@@ -568,6 +581,7 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         LH_TRACED(ctx, "k_spgemm_gather", k_spgemm_gather<<<grid, T, 0, ctx->stream>>>(n0, tmp_off, r->c_off, tcol, tval, r->c_col, r->c_val));
 #undef STEP
     lh_free(ctx, ub); lh_free(ctx, cnt); lh_free(ctx, tmp_off); lh_free(ctx, gcap); lh_free(ctx, goff);
+    lh_free(ctx, n_hash);
     lh_free(ctx, tcol); lh_free(ctx, tval); lh_free(ctx, gkey); lh_free(ctx, ghi); lh_free(ctx, glo);
     if (s == LH_OK) {
         cudaError_t e = cudaGetLastError();
