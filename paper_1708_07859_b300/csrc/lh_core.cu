@@ -311,9 +311,7 @@ lh_status lh_scan_u64_to_u64(lh_ctx *ctx, const uint64_t *in, uint64_t *out, uin
 // ---------------------------------------------------------------- radix sort
 // LSD, 8-bit digits.  Per pass: per-tile digit histograms (digit-major, so
 // one exclusive scan gives every (digit, tile) its output base), then a
-// stable scatter.  Within a tile, keys are ranked in rounds of 256: lanes
-// with equal digits are grouped by __match_any_sync, warps are ordered by a
-// per-digit prefix over warps, rounds by a running per-digit count.
+// stable scatter that ranks each tile's keys in shared memory.
 
 namespace {
 
@@ -326,38 +324,81 @@ __global__ void k_sort_hist(const uint64_t *keys, uint64_t n, int shift, uint32_
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
-    uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    uint32_t d[kSortRounds];
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
-        uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+        const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
+        d[r] = i < n ? (uint32_t)((keys[i] >> shift) & 255u) : 256u;
     }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r)
+        if (d[r] < 256u) atomicAdd(&h[d[r]], 1u);
     __syncthreads();
     hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter of one tile: keys are ranked per digit (warp match + prefix
-// over warps + running count over rounds), placed in shared memory grouped by
-// digit, and written out as contiguous per-digit runs so that consecutive
-// threads store consecutive addresses.
+// Stable scatter of one tile.  Warp w ranks the tile's keys
+// [w*512, (w+1)*512) in 16 rounds of 32 with warp-private digit counters
+// (lanes with equal digits are grouped by __match_any_sync; the group's
+// leader reads and advances the counter), so ranking needs no block barrier.
+// One prefix over warps and digits then turns the counters into each
+// (warp, digit) start in shared memory, where keys are placed grouped by
+// digit and written out as contiguous per-digit runs.
 constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
+constexpr int kSortWarps = kSortThreads / 32;
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t n,
-                                                               int shift, const uint32_t *hist, const uint64_t *offs,
-                                                               uint32_t ntiles, uint64_t *kout, uint32_t *vout) {
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t n,
+                                                               int shift, const uint64_t *offs, uint32_t ntiles,
+                                                               uint64_t *kout, uint32_t *vout) {
     extern __shared__ uint64_t s_keys[];                       // kSortTile keys, grouped by digit
     uint32_t *s_vals = (uint32_t *)(s_keys + kSortTile);      // their payloads
-    __shared__ uint32_t wcnt[kSortThreads / 32][256];
-    __shared__ uint32_t running[256];
-    __shared__ uint32_t round_tot[256];
+    __shared__ uint32_t wcnt[kSortWarps][256];                // per-warp digit counts, then starts
     __shared__ uint32_t lstart[256];
-    __shared__ uint32_t wtot[kSortThreads / 32];
+    __shared__ uint32_t wtot[kSortWarps];
     __shared__ uint64_t gbase[256];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][t] = 0;
     gbase[t] = offs[(uint64_t)t * ntiles + blockIdx.x];
-    running[t] = 0;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint64_t tbase = (uint64_t)blockIdx.x * kSortTile;
+    const uint32_t tile_n = (uint32_t)min((uint64_t)kSortTile, n - tbase);
+    const uint64_t wbase = tbase + (uint64_t)warp * (kSortRounds * 32);
+    // all of this thread's keys are loaded up front: one memory latency per tile
+    uint64_t kr[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+        kr[r] = i < n ? kin[i] : 0;
+    }
+    __syncthreads();
+    uint32_t rk[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const bool valid = wbase + (uint64_t)r * 32 + lane < n;
+        const uint32_t d = valid ? (uint32_t)((kr[r] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(LH_FULL, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (valid && lane == leader) {
+            before = wcnt[warp][d];
+            wcnt[warp][d] = before + __popc(peers);
+        }
+        rk[r] = __shfl_sync(LH_FULL, before, leader) + __popc(peers & lt_mask);
+        __syncwarp();
+    }
+    __syncthreads();
     {
-        // exclusive prefix of this tile's digit counts: each digit's run start in shared memory
-        const uint32_t c = hist[(uint64_t)t * ntiles + blockIdx.x];
+        // thread t owns digit t: exclusive prefix over warps, then over digits
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t x = wcnt[w][t];
+            wcnt[w][t] = c;
+            c += x;
+        }
         uint32_t incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -368,53 +409,31 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *k
         __syncthreads();
         uint32_t wp = 0;
         for (int w = 0; w < warp; ++w) wp += wtot[w];
-        lstart[t] = wp + incl - c;
+        const uint32_t start = wp + incl - c;
+        lstart[t] = start;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) wcnt[w][t] += start;
     }
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
-    const uint32_t tile_n = (uint32_t)min((uint64_t)kSortTile, n - base);
-    // all of this thread's keys are loaded up front: one memory latency per tile
-    uint64_t kr[kSortRounds];
+    __syncthreads();
+    // keys go to their slots first; the payloads are loaded only now, when
+    // the keys' registers are free, and follow them
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        if (wbase + (uint64_t)r * 32 + lane < n) {
+            const uint32_t d = (uint32_t)((kr[r] >> shift) & 255u);
+            rk[r] += wcnt[warp][d];
+            s_keys[rk[r]] = kr[r];
+        }
+    }
     uint32_t vr[kSortRounds];
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
-        const uint64_t i = base + (uint64_t)r * kSortThreads + t;
-        kr[r] = i < n ? kin[i] : 0;
+        const uint64_t i = wbase + (uint64_t)r * 32 + lane;
         vr[r] = i < n ? vin[i] : 0;
     }
 #pragma unroll
-    for (int r = 0; r < kSortRounds; ++r) {
-#pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
-        __syncthreads();
-        const uint64_t i = base + (uint64_t)r * kSortThreads + t;
-        const bool valid = i < n;
-        const uint64_t k = kr[r];
-        const uint32_t v = vr[r];
-        const uint32_t d = valid ? (uint32_t)((k >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(LH_FULL, d);
-        const uint32_t rk = __popc(peers & lt_mask);
-        if (valid && rk == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t p = 0;
-#pragma unroll
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                const uint32_t c = wcnt[w][t];
-                wcnt[w][t] = p;
-                p += c;
-            }
-            round_tot[t] = p;
-        }
-        __syncthreads();
-        if (valid) {
-            const uint32_t at = lstart[d] + running[d] + wcnt[warp][d] + rk;
-            s_keys[at] = k;
-            s_vals[at] = v;
-        }
-        __syncthreads();
-        running[t] += round_tot[t];
-    }
+    for (int r = 0; r < kSortRounds; ++r)
+        if (wbase + (uint64_t)r * 32 + lane < n) s_vals[rk[r]] = vr[r];
     __syncthreads();
     for (uint32_t at = t; at < tile_n; at += kSortThreads) {
         const uint64_t k = s_keys[at];
@@ -454,7 +473,7 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_
         s = lh_scan_u32_to_u64(ctx, hist, offs, (uint64_t)256 * ntiles);
         if (s != LH_OK) break;
         LH_TRACED(ctx, "k_sort_scatter", k_sort_scatter<<<ntiles, kSortThreads, kScatterSmem, ctx->stream>>>(
-                                             ka, va, n, shift, hist, offs, ntiles, kb, vb));
+                                             ka, va, n, shift, offs, ntiles, kb, vb));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort: %s", cudaGetErrorString(e));
         uint64_t *tk = ka; ka = kb; kb = tk;

@@ -281,15 +281,15 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm_numeric(
 // the concatenated B rows into registers as 64-bit keys (k << 8 | product
 // index); a bitonic network over the 256 positions p = 8 * lane + e sorts
 // them (register compare-exchanges for distances < 8, shuffles for larger
-// ones); equal k are then adjacent and each run is summed with compensated
-// fp32 arithmetic and written once, already in ascending k.
+// ones); equal k are then adjacent.  Runs are summed in registers with
+// compensated fp32 arithmetic: each lane sums its 8 positions, and a
+// segmented suffix scan over lanes carries a run across lane boundaries.
+// Each run is written once, already in ascending k.
 constexpr uint32_t kEscPairs = 256;
 constexpr int kEscWarps = 8;
 
 struct EscSmem {
     float2 val[kEscPairs];
-    uint32_t skey[kEscPairs + kEscPairs / 32];
-    uint8_t sidx[kEscPairs + kEscPairs / 32];
     uint32_t jb[32], jl[32], jp[32];
     float ja[32];
 };
@@ -335,13 +335,13 @@ __device__ __forceinline__ void esc_sort256(K (&key)[8], uint32_t lane) {
     }
 }
 
-// shared index of sorted position p: one skew word per 32 so that lanes
-// reading p = 8 * lane + e hit distinct banks
-__device__ __forceinline__ uint32_t esc_sk(uint32_t p) { return p + (p >> 5); }
+// shared slot of product t = 8 * lane + e: lane-major, so the expand
+// phase's stores of one e hit 32 consecutive float2
+__device__ __forceinline__ uint32_t esc_vslot(uint32_t t) { return ((t & 7u) << 5) | (t >> 3); }
 
 // K = uint32_t when every k < 2^24 (k << 8 | index fits 32 bits), else uint64_t.
 template <class K>
-__global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
+__global__ void __launch_bounds__(kEscWarps * 32, 6) k_spgemm_esc(
     DTrie A, const float *av, DTrie B, const float *bv, uint32_t nA0, const uint32_t *ub,
     const uint64_t *tmp_off, uint32_t *tcol, float *tval, uint32_t *cnt) {
     __shared__ EscSmem sm_all[kEscWarps];
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
                     const uint32_t pos = S.jb[r] + off;
                     float ph, pl;
                     lh_two_prod(S.ja[r], __ldg(bv + pos), ph, pl);
-                    S.val[t] = make_float2(ph, pl);
+                    S.val[esc_vslot(t)] = make_float2(ph, pl);
                     key[e] = ((K)__ldg(B.lv[1].vals + pos) << 8) | t;
                 }
             }
@@ -423,26 +423,26 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
                     const uint32_t pos = S.jb[lo] + (t - (S.jp[lo] - S.jl[lo]));
                     float ph, pl;
                     lh_two_prod(S.ja[lo], __ldg(bv + pos), ph, pl);
-                    S.val[t] = make_float2(ph, pl);
+                    S.val[esc_vslot(t)] = make_float2(ph, pl);
                     key[e] = ((K)__ldg(B.lv[1].vals + pos) << 8) | t;
                 }
             }
             esc_sort256(key, lane);
         }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const uint32_t ps = esc_sk((lane << 3) + e);
-            S.skey[ps] = (uint32_t)(key[e] >> 8);
-            S.sidx[ps] = (uint8_t)(key[e] & 255u);
-        }
         __syncwarp();
-        // runs of equal k: the first position of a run sums it
-        uint32_t heads = 0;
+        // runs of equal k, in registers: sorted position 8 * lane + e holds key[e]
+        uint32_t col[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) col[e] = (uint32_t)(key[e] >> 8);
+        const uint32_t prev_last = __shfl_up_sync(LH_FULL, col[7], 1);
+        uint32_t hmask = 0;  // bit e: position 8 * lane + e opens a run
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint32_t ps = (lane << 3) + e;
-            heads += (ps < total && (ps == 0 || S.skey[esc_sk(ps)] != S.skey[esc_sk(ps - 1)])) ? 1u : 0u;
+            const uint32_t prev = e ? col[e - 1] : prev_last;
+            if (ps < total && (ps == 0 || col[e] != prev)) hmask |= 1u << e;
         }
+        const uint32_t heads = __popc(hmask);
         uint32_t hincl = heads;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -451,20 +451,54 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_spgemm_esc(
         }
         uint32_t oi = hincl - heads;
         const uint64_t t0 = tmp_off[p];
+        // within the lane: runs it opens and closes are written at once; the
+        // part before its first head is its lead, the open run its trail
+        float ah = 0.f, al = 0.f, lead_h = 0.f, lead_l = 0.f;
+        uint32_t rc = 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const uint32_t ps = (lane << 3) + e;
-            if (ps < total && (ps == 0 || S.skey[esc_sk(ps)] != S.skey[esc_sk(ps - 1)])) {
-                const uint32_t kk = S.skey[esc_sk(ps)];
-                float sh = 0.f, sl = 0.f;
-                for (uint32_t r = ps; r < total && S.skey[esc_sk(r)] == kk; ++r) {
-                    const float2 v = S.val[S.sidx[esc_sk(r)]];
-                    lh_pair_add(sh, sl, v.x, v.y);
+            float2 v = make_float2(0.f, 0.f);
+            if ((lane << 3) + e < total) v = S.val[esc_vslot((uint32_t)(key[e] & 255u))];
+            if ((hmask >> e) & 1u) {
+                if (hmask & ((1u << e) - 1u)) {
+                    tcol[t0 + oi] = rc;
+                    tval[t0 + oi] = ah + al;
+                    ++oi;
+                } else {
+                    lead_h = ah;
+                    lead_l = al;
                 }
-                tcol[t0 + oi] = kk;
-                tval[t0 + oi] = sh + sl;
-                ++oi;
+                rc = col[e];
+                ah = v.x;
+                al = v.y;
+            } else {
+                lh_pair_add(ah, al, v.x, v.y);
             }
+        }
+        if (!hmask) {
+            lead_h = ah;
+            lead_l = al;
+        }
+        // segmented suffix sum of leads: q(L) = lead(L) + lead(L+1) + ... up to
+        // and including the first lane at or after L that opens a run
+        float qh = lead_h, ql = lead_l;
+        int stop = hmask != 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float oh = __shfl_down_sync(LH_FULL, qh, o);
+            const float ol = __shfl_down_sync(LH_FULL, ql, o);
+            const int ostop = __shfl_down_sync(LH_FULL, stop, o);
+            if (lane + o < 32 && !stop) {
+                lh_pair_add(qh, ql, oh, ol);
+                stop = ostop;
+            }
+        }
+        // the lane's open run continues through the leads of the lanes after it
+        float rh = __shfl_down_sync(LH_FULL, qh, 1), rl = __shfl_down_sync(LH_FULL, ql, 1);
+        if (hmask) {
+            if (lane < 31) lh_pair_add(ah, al, rh, rl);
+            tcol[t0 + oi] = rc;
+            tval[t0 + oi] = ah + al;
         }
         if (lane == 31) cnt[p] = hincl;
         __syncwarp();
@@ -478,9 +512,24 @@ __global__ void k_spgemm_gather(uint32_t nA0, const uint64_t *tmp_off, const uin
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t p = gw; p < nA0; p += nw) {
         const uint64_t s0 = tmp_off[p], d0 = c_off[p], n = c_off[p + 1] - d0;
-        for (uint64_t s = lane; s < n; s += 32) {
-            ccol[d0 + s] = tcol[s0 + s];
-            cval[d0 + s] = tval[s0 + s];
+        // four strided positions per lane: all loads issued before the stores
+        for (uint64_t s = lane; s < n; s += 128) {
+            uint32_t c[4];
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t i = s + 32 * u;
+                c[u] = i < n ? tcol[s0 + i] : 0u;
+                v[u] = i < n ? tval[s0 + i] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t i = s + 32 * u;
+                if (i < n) {
+                    ccol[d0 + i] = c[u];
+                    cval[d0 + i] = v[u];
+                }
+            }
         }
     }
 }

@@ -85,6 +85,28 @@ def test_spgemm_small(ctx, orc, lhlib, shape):
     check_rows(orc, A, nA, B, nB, nC, rows, off, cols, vals, np.arange(rows.size))
 
 
+def test_spgemm_mixed_row_kinds(ctx, orc, lhlib):
+    """Sort rows (uniform and ragged B rows), hash rows (more than 32 A
+    entries, or more than 256 products), rows whose products are all missing
+    and empty A rows, interleaved by row id: the rows are written in row order
+    whatever kernel summed them."""
+    nB, nC = 400, 300
+    parts = []
+    for i, k in enumerate((3, 40, 12, 1, 33, 2)):
+        r, c, v = gen.uniform_coo(120, nB, k, 50 + i)
+        parts.append((r * 7 + i, c, v))          # row ids 7r + i; 7r + 6 stay empty
+    A = tuple(np.concatenate(x) for x in zip(*parts))
+    r16, c16, v16 = gen.uniform_coo(200, nC, 16, 60)   # B rows 0..199: 16 entries
+    r24, c24, v24 = gen.uniform_coo(120, nC, 24, 61)   # B rows 280..399: 24 entries
+    B = (np.concatenate([r16, r24 + 280]).astype(np.uint32), np.concatenate([c16, c24]),
+         np.concatenate([v16, v24]))                    # B rows 200..279 missing
+    nA = 7 * 120
+    rows, off, cols, vals = spgemm(ctx, lhlib, A, B)
+    assert np.array_equal(rows, np.unique(A[0]))
+    check_rows(orc, A, nA, B, nB, nC, rows, off, cols, vals, np.arange(rows.size))
+    assert np.all(np.diff(off.astype(np.int64)) >= 0)
+
+
 def test_spgemm_identity_and_permutation_exact(ctx, lhlib):
     A = gen.uniform_coo(300, 200, 9, 43)
     I = (np.arange(200), np.arange(200), np.ones(200, np.float32))
