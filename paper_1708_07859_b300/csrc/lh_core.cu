@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
 
 }  // namespace
 
-lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_t *tmp_k,
-                            uint32_t *tmp_v, uint64_t n, int bits) {
+lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint64_t **tmp_k,
+                            uint32_t **tmp_v, uint64_t n, int bits) {
     if (n <= 1 || bits <= 0) return LH_OK;
     uint64_t ntiles64 = (n + kSortTile - 1) / kSortTile;
     if (ntiles64 > (1u << 24)) return lh_fail(ctx, LH_EUNSUPPORTED, "sort: too many keys");
@@ -464,8 +464,8 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_
         cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort smem attribute: %s", cudaGetErrorString(e));
     }
-    uint64_t *ka = keys, *kb = tmp_k;
-    uint32_t *va = vals, *vb = tmp_v;
+    uint64_t *ka = *keys, *kb = *tmp_k;
+    uint32_t *va = *vals, *vb = *tmp_v;
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes && s == LH_OK; ++p) {
         int shift = 8 * p;
@@ -479,14 +479,11 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    if (s == LH_OK && ka != keys) {
-        cudaError_t e = cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
-                                        ctx->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
-                                ctx->stream);
-        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort copy: %s", cudaGetErrorString(e));
-    }
+    // the sorted data stays where the last pass wrote it: hand back the buffers
+    *keys = ka;
+    *tmp_k = kb;
+    *vals = va;
+    *tmp_v = vb;
     lh_free(ctx, hist);
     lh_free(ctx, offs);
     return s;

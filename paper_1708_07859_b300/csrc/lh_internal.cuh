@@ -111,9 +111,11 @@ lh_status lh_scan_u64_to_u64(lh_ctx *ctx, const uint64_t *in, uint64_t *out, uin
 // ----------------------------------------------------------------- radix sort
 
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.
-// The sorted pairs end in (keys, vals); (tmp_k, tmp_v) are scratch of length n.
-lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t *keys, uint32_t *vals, uint64_t *tmp_k,
-                            uint32_t *tmp_v, uint64_t n, int bits);
+// (*keys, *vals) hold the input and (*tmp_k, *tmp_v) scratch of length n; on
+// return the pointers are swapped as needed so that (*keys, *vals) hold the
+// sorted pairs and (*tmp_k, *tmp_v) the scratch.
+lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint64_t **tmp_k,
+                            uint32_t **tmp_v, uint64_t n, int bits);
 
 // ----------------------------------------------------------------------- tries
 

@@ -7,77 +7,230 @@
 
 namespace {
 
-__global__ void k_col_max(const uint32_t *col, uint64_t n, uint32_t *out) {
-    uint32_t m = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        m = max(m, col[i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(LH_FULL, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
-}
-
 struct PackArgs {
     const uint32_t *col[LH_MAX_LEVELS];
     uint32_t shift[LH_MAX_LEVELS];
     uint32_t nlev;
+    const uint32_t *payload;  // 4-byte annotation carried through the sort, or null: row ids
 };
 
+// Largest value of every key column, one launch: each thread takes four
+// rows per grid stride, all loads issued before the maxima.
+__global__ void k_col_max(PackArgs a, uint64_t n, uint32_t *out) {
+    uint32_t m[LH_MAX_LEVELS] = {0};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+#pragma unroll
+        for (int l = 0; l < LH_MAX_LEVELS; ++l) {
+            if (l >= (int)a.nlev) break;
+            uint32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = i + u * stride < n ? a.col[l][i + u * stride] : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) m[l] = max(m[l], v[u]);
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < LH_MAX_LEVELS; ++l) {
+        if (l >= (int)a.nlev) break;
+        uint32_t x = m[l];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(LH_FULL, x, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(out + l, x);
+    }
+}
+
+// Packed key (level 0 in the high bits) and sort payload of every row; four
+// rows per thread and grid stride, loaded before they are stored.
 __global__ void k_pack(PackArgs a, uint64_t n, uint64_t *key, uint32_t *rid) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k = 0;
-        for (uint32_t l = 0; l < a.nlev; ++l) k |= (uint64_t)a.col[l][i] << a.shift[l];
-        key[i] = k;
-        rid[i] = (uint32_t)i;
-    }
-}
-
-// head flags of distinct keys
-__global__ void k_heads(const uint64_t *key, uint64_t n, uint32_t *flag) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
-}
-
-// compact distinct keys; runstart[u] = first sorted row of distinct tuple u
-__global__ void k_compact_unique(const uint64_t *key, const uint32_t *flag, const uint64_t *pos,
-                                 uint64_t n, uint64_t *ukey, uint64_t *runstart) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        if (flag[i]) {
-            ukey[pos[i]] = key[i];
-            runstart[pos[i]] = i;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+        uint64_t k[4] = {0, 0, 0, 0};
+        uint32_t r[4];
+#pragma unroll
+        for (int l = 0; l < LH_MAX_LEVELS; ++l) {
+            if (l >= (int)a.nlev) break;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * stride < n) k[u] |= (uint64_t)a.col[l][i + u * stride] << a.shift[l];
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            r[u] = i + u * stride < n ? (a.payload ? a.payload[i + u * stride] : (uint32_t)(i + u * stride)) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i + u * stride < n) {
+                key[i + u * stride] = k[u];
+                rid[i + u * stride] = r[u];
+            }
+    }
 }
 
-// per-level prefix-boundary flags over distinct keys
-__global__ void k_level_flags(const uint64_t *ukey, uint64_t nu, uint32_t pshift, uint32_t *flag) {
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu;
-         u += (uint64_t)gridDim.x * blockDim.x) {
-        bool h = (u == 0);
-        if (!h) {
-            uint64_t a = pshift >= 64 ? 0 : (ukey[u] >> pshift);
-            uint64_t b = pshift >= 64 ? 0 : (ukey[u - 1] >> pshift);
-            h = a != b;
+// ---- CSR levels from the sorted packed keys, in one pass ------------------
+// Level l's prefix of key k is k >> shift[l] (levels 0..l); a sorted row i
+// opens a level-l entry when that prefix differs from row i-1's.  A tile of
+// 2048 rows is staged in shared memory; thread t takes rows j * 256 + t, so
+// the entries a warp opens for one j land at consecutive indices (ballot +
+// popc) and its stores coalesce.  Warp l scans the tile's per-(j, warp)
+// counts of level l, finds the tile's offset in level l by decoupled
+// look-back over tile tickets, and then every opened entry writes its value,
+// its first child's index in the level below and (leaf level) the first
+// sorted row of its distinct key.  Tiles are ticketed in order, so every
+// tile a tile waits on is already running and publishes its count without
+// waiting.
+constexpr int kLvThreads = 256;
+constexpr int kLvWarps = kLvThreads / 32;
+constexpr int kLvItems = 8;
+constexpr uint64_t kLvTile = (uint64_t)kLvThreads * kLvItems;
+constexpr unsigned long long kLvAgg = 1ull << 62, kLvInc = 1ull << 63, kLvVal = (1ull << 62) - 1;
+constexpr uint32_t kLvSpins = 1u << 20;
+
+struct LevelArgs {
+    uint32_t nlev;
+    uint32_t shift[LH_MAX_LEVELS];
+    uint32_t vmask[LH_MAX_LEVELS];
+    uint32_t *vals[LH_MAX_LEVELS];  // capacity n each
+    uint32_t *offs[LH_MAX_LEVELS];  // levels 0..nlev-2, capacity n + 1 each
+    uint32_t *runstart;             // capacity n
+    unsigned long long *state;      // [tiles][nlev], zeroed
+    uint32_t *ticket;               // zeroed
+    uint64_t *count;                // [nlev]: entries per level
+    uint32_t *status;
+};
+
+__device__ __forceinline__ void lv_store(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long lv_load(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int NL>
+__global__ void __launch_bounds__(kLvThreads) k_levels(const uint64_t *key, uint64_t n, LevelArgs a) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_ok;
+    __shared__ uint64_t s_k[kLvTile];
+    __shared__ uint32_t s_base[NL][kLvItems * kLvWarps];  // per (j, warp) counts, then exclusive bases
+    __shared__ uint64_t s_agg[NL];
+    __shared__ uint64_t s_off[NL];
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    if (t == 0) {
+        s_tile = atomicAdd(a.ticket, 1u);
+        s_ok = 1;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t tb = (uint64_t)tile * kLvTile;
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) {
+        const uint32_t r = j * kLvThreads + t;
+        s_k[r] = tb + r < n ? key[tb + r] : 0;
+    }
+    const uint64_t before_tile = (tb > 0 && tb <= n) ? key[tb - 1] : 0;
+    __syncthreads();
+    // bal[l][j] bit lane: row j * 256 + 32 * warp + lane opens a level-l entry
+    uint32_t bal[NL][kLvItems];
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) {
+        const uint32_t r = j * kLvThreads + t;
+        const uint64_t i = tb + r;
+        const uint64_t k = s_k[r], pk = r ? s_k[r - 1] : before_tile;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const bool open = i < n && (i == 0 || (k >> a.shift[l]) != (pk >> a.shift[l]));
+            bal[l][j] = __ballot_sync(LH_FULL, open);
+            if (lane == 0) s_base[l][j * kLvWarps + warp] = __popc(bal[l][j]);
         }
-        flag[u] = h ? 1u : 0u;
+    }
+    __syncthreads();
+    if (warp < NL) {
+        const uint32_t l = warp;
+        // exclusive scan of the 64 (j, warp) counts in row order; lane holds two
+        const uint32_t c0 = s_base[l][2 * lane], c1 = s_base[l][2 * lane + 1];
+        uint32_t incl = c0 + c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(LH_FULL, incl, o);
+            if (lane >= o) incl += x;
+        }
+        const uint32_t ex = incl - c0 - c1;
+        s_base[l][2 * lane] = ex;
+        s_base[l][2 * lane + 1] = ex + c0;
+        const uint64_t agg = __shfl_sync(LH_FULL, incl, 31);
+        // publish the tile's count, then look back for its offset
+        if (lane == 0) lv_store(a.state + (uint64_t)tile * NL + l, (tile == 0 ? kLvInc : kLvAgg) | agg);
+        uint64_t excl = 0;
+        int64_t q = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        bool ok = true;
+        while (q >= 0) {
+            const int64_t qi = q - (int64_t)lane;
+            const unsigned long long w = qi >= 0 ? lv_load(a.state + (uint64_t)qi * NL + l) : kLvInc;
+            const uint32_t inc = __ballot_sync(LH_FULL, (w & kLvInc) != 0);
+            const uint32_t ready = __ballot_sync(LH_FULL, (w >> 62) != 0);
+            const uint32_t fi = inc ? (uint32_t)__ffs(inc) - 1 : 31u;
+            const uint32_t need = fi == 31 ? LH_FULL : ((2u << fi) - 1u);
+            if ((ready & need) != need) {
+                if (++spins >= kLvSpins) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            uint64_t v = lane <= fi ? (uint64_t)(w & kLvVal) : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LH_FULL, v, o);
+            excl += v;
+            if (inc) break;
+            q -= 32;
+        }
+        if (lane == 0) {
+            if (!ok) {
+                lh_set_status(a.status, LH_ETIMEOUT);
+                s_ok = 0;
+            }
+            s_off[l] = excl;
+            s_agg[l] = agg;
+            if (tile > 0) lv_store(a.state + (uint64_t)tile * NL + l, kLvInc | ((excl + agg) & kLvVal));
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) {
+        const uint32_t r = j * kLvThreads + t;
+        const uint64_t i = tb + r;
+        if (i >= n) break;
+        const uint64_t k = s_k[r];
+        uint64_t pp = 0;  // index of the entry this row opens one level up
+        bool popen = false;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const bool open = (bal[l][j] >> lane) & 1u;
+            if (open) {
+                const uint64_t p = s_off[l] + s_base[l][j * kLvWarps + warp] + __popc(bal[l][j] & lt_mask);
+                a.vals[l][p] = (uint32_t)(k >> a.shift[l]) & a.vmask[l];
+                if (popen) a.offs[l - 1][pp] = (uint32_t)p;
+                if (l + 1 == NL) a.runstart[p] = (uint32_t)i;
+                pp = p;
+            }
+            popen = open;
+        }
+        if (i + 1 == n) {
+            // the last row closes every level: entry counts and the final offsets
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const uint64_t c = s_off[l] + s_agg[l];
+                a.count[l] = c;
+                if (l > 0) a.offs[l - 1][s_off[l - 1] + s_agg[l - 1]] = (uint32_t)c;
+            }
+        }
     }
 }
-
-__global__ void k_level_emit(const uint64_t *ukey, uint64_t nu, const uint32_t *flag,
-                             const uint32_t *pos, uint32_t vshift, uint64_t vmask, uint32_t *vals,
-                             const uint32_t *pflag, const uint32_t *ppos, uint32_t *poffs) {
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu;
-         u += (uint64_t)gridDim.x * blockDim.x) {
-        if (!flag[u]) continue;
-        uint32_t p = pos[u];
-        vals[p] = (uint32_t)((ukey[u] >> vshift) & vmask);
-        if (pflag && pflag[u]) poffs[ppos[u]] = p;  // first child of the parent entry
-    }
-}
-
-__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 
 // --- annotations -----------------------------------------------------------
 
@@ -101,7 +254,7 @@ struct AnnoArgs {
 
 // One thread per distinct tuple merges the rows of its run (sorted row ids
 // rid[runstart[u] .. runstart[u+1])) in sorted order.
-__global__ void k_annos(AnnoArgs a, const uint32_t *rid, const uint64_t *runstart, uint64_t nu,
+__global__ void k_annos(AnnoArgs a, const uint32_t *rid, const uint32_t *runstart, uint64_t nu,
                         uint64_t n) {
     for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu;
          u += (uint64_t)gridDim.x * blockDim.x) {
@@ -142,6 +295,25 @@ __global__ void k_annos(AnnoArgs a, const uint32_t *rid, const uint64_t *runstar
                     ((double *)a.out[c])[u] = s;
                 }
             }
+        }
+    }
+}
+
+// Leaf-order annotation when the (single, 4-byte) annotation rode through
+// the sort as its payload: run u covers sorted rows runstart[u] ..
+// runstart[u+1]; FIRST takes the run's first row (the sort is stable), SUM
+// adds the run in row order.
+__global__ void k_annos_carried(const uint32_t *payload, const uint32_t *runstart, uint64_t nu, uint64_t n,
+                                uint32_t sum_f32, uint32_t *out) {
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu;
+         u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r0 = runstart[u], r1 = (u + 1 < nu) ? runstart[u + 1] : n;
+        if (!sum_f32) {
+            out[u] = payload[r0];
+        } else {
+            float s = 0.f;
+            for (uint64_t r = r0; r < r1; ++r) s += __uint_as_float(payload[r]);
+            out[u] = __float_as_uint(s);
         }
     }
 }
@@ -434,28 +606,33 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     const uint64_t n = rel->nrows;
     const unsigned T = 256;
     const unsigned G = (unsigned)std::min<uint64_t>(lh_blocks(n, T), (uint64_t)ctx->num_sms * 16);
+    const unsigned G4 = (unsigned)std::min<uint64_t>(lh_blocks((n + 3) / 4, T), (uint64_t)ctx->num_sms * 16);
 
-    uint32_t *d_max = nullptr;
-    uint64_t *key = nullptr, *tkey = nullptr, *ukey = nullptr, *runstart = nullptr, *upos = nullptr;
-    uint32_t *rid = nullptr, *trid = nullptr, *flag = nullptr;
-    std::vector<uint32_t *> lflag(L, nullptr), lpos(L, nullptr);
+    uint32_t *d_max = nullptr, *ticket = nullptr;
+    uint64_t *key = nullptr, *tkey = nullptr, *d_count = nullptr;
+    uint32_t *rid = nullptr, *trid = nullptr, *runstart = nullptr;
+    unsigned long long *lstate = nullptr;
+    std::vector<uint32_t *> tvals(L, nullptr), toffs(L, nullptr);
     uint64_t nu = 0;
     lh_status s = LH_OK;
     auto cleanup_tmp = [&]() {
-        lh_free(ctx, d_max); lh_free(ctx, key); lh_free(ctx, tkey); lh_free(ctx, ukey);
-        lh_free(ctx, runstart); lh_free(ctx, upos); lh_free(ctx, rid); lh_free(ctx, trid);
-        lh_free(ctx, flag);
-        for (uint32_t l = 0; l < L; ++l) { lh_free(ctx, lflag[l]); lh_free(ctx, lpos[l]); }
+        lh_free(ctx, d_max); lh_free(ctx, ticket); lh_free(ctx, key); lh_free(ctx, tkey);
+        lh_free(ctx, d_count); lh_free(ctx, rid); lh_free(ctx, trid); lh_free(ctx, runstart);
+        lh_free(ctx, lstate);
+        for (uint32_t l = 0; l < L; ++l) { lh_free(ctx, tvals[l]); lh_free(ctx, toffs[l]); }
     };
 #define STEP(x) if (s == LH_OK) s = (x)
     // 1. key widths
     uint32_t bits[LH_MAX_LEVELS] = {0};
     uint32_t total_bits = 0;
+    PackArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.nlev = L;
+    for (uint32_t l = 0; l < L; ++l) pa.col[l] = rel->keys[key_order[l]];
     STEP(lh_alloc(ctx, &d_max, L));
     if (s == LH_OK) {
         cudaMemsetAsync(d_max, 0, L * sizeof(uint32_t), ctx->stream);
-        for (uint32_t l = 0; l < L && n; ++l)
-            LH_TRACED(ctx, "k_col_max", k_col_max<<<G, T, 0, ctx->stream>>>(rel->keys[key_order[l]], n, d_max + l));
+        if (n) LH_TRACED(ctx, "k_col_max", k_col_max<<<G4, T, 0, ctx->stream>>>(pa, n, d_max));
         uint32_t hmax[LH_MAX_LEVELS] = {0};
         STEP(lh_readback(ctx, d_max, L * sizeof(uint32_t), hmax));
         for (uint32_t l = 0; l < L; ++l) {
@@ -467,9 +644,6 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
             s = lh_fail(ctx, LH_EUNSUPPORTED, "packed key needs %u > 64 bits", total_bits);
     }
     // 2. pack + sort
-    PackArgs pa;
-    memset(&pa, 0, sizeof(pa));
-    pa.nlev = L;
     uint32_t shift[LH_MAX_LEVELS];
     {
         uint32_t acc = 0;
@@ -477,53 +651,108 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
             shift[l] = acc;
             acc += bits[l];
         }
-        for (uint32_t l = 0; l < L; ++l) {
-            pa.col[l] = rel->keys[key_order[l]];
-            pa.shift[l] = shift[l];
-        }
+        for (uint32_t l = 0; l < L; ++l) pa.shift[l] = shift[l];
     }
+    // one 4-byte FIRST / f32 SUM annotation is sorted along with the keys
+    // instead of the row ids, so leaf order needs no gather through them
+    const bool carry = rel->nannos == 1 && dtype_size(rel->anno_types[0]) == 4 &&
+                       (merge == LH_MERGE_FIRST || (merge == LH_MERGE_SUM && rel->anno_types[0] == LH_T_F32));
+    pa.payload = carry ? (const uint32_t *)rel->annos[0] : nullptr;
     STEP(lh_alloc(ctx, &key, n));
     STEP(lh_alloc(ctx, &tkey, n));
     STEP(lh_alloc(ctx, &rid, n));
     STEP(lh_alloc(ctx, &trid, n));
-    STEP(lh_alloc(ctx, &flag, n));
-    STEP(lh_alloc(ctx, &upos, n + 1));
     if (s == LH_OK && n) {
-        LH_TRACED(ctx, "k_pack", k_pack<<<G, T, 0, ctx->stream>>>(pa, n, key, rid));
-        STEP(lh_radix_sort_u64(ctx, key, rid, tkey, trid, n, (int)total_bits));
-        if (s == LH_OK) LH_TRACED(ctx, "k_heads", k_heads<<<G, T, 0, ctx->stream>>>(key, n, flag));
-        STEP(lh_scan_u32_to_u64(ctx, flag, upos, n));
-        STEP(lh_readback(ctx, upos + n, sizeof(uint64_t), &nu));
+        LH_TRACED(ctx, "k_pack", k_pack<<<G4, T, 0, ctx->stream>>>(pa, n, key, rid));
+        STEP(lh_radix_sort_u64(ctx, &key, &rid, &tkey, &trid, n, (int)total_bits));
     }
-    STEP(lh_alloc(ctx, &ukey, nu));
-    STEP(lh_alloc(ctx, &runstart, nu));
-    if (s == LH_OK && n) LH_TRACED(ctx, "k_compact_unique", k_compact_unique<<<G, T, 0, ctx->stream>>>(key, flag, upos, n, ukey, runstart));
-    // 3. levels
-    for (uint32_t l = 0; l < L && s == LH_OK; ++l) {
-        STEP(lh_alloc(ctx, &lflag[l], nu));
-        STEP(lh_alloc(ctx, &lpos[l], nu + 1));
-        if (s != LH_OK) break;
-        if (nu) LH_TRACED(ctx, "k_level_flags", k_level_flags<<<G, T, 0, ctx->stream>>>(ukey, nu, shift[l], lflag[l]));
-        STEP(lh_scan_u32_to_u32(ctx, lflag[l], lpos[l], nu));
-        uint32_t nl = 0;
-        STEP(lh_readback(ctx, lpos[l] + nu, sizeof(uint32_t), &nl));
-        t->lv[l].n = nu ? nl : 0;
+    // 3. levels: the leaf level is written in place (capacity n), the levels
+    //    above into temporaries, copied out once their sizes are known
+    const uint64_t ntiles = (n + kLvTile - 1) / kLvTile;
+    STEP(trie_alloc(ctx, t, &t->lv[L - 1].vals, n));
+    STEP(lh_alloc(ctx, &runstart, n));
+    STEP(lh_alloc(ctx, &d_count, L));
+    STEP(lh_alloc(ctx, &ticket, 1));
+    STEP(lh_alloc(ctx, &lstate, ntiles * L));
+    for (uint32_t l = 0; l + 1 < L; ++l) {
+        STEP(lh_alloc(ctx, &tvals[l], n));
+        STEP(lh_alloc(ctx, &toffs[l], n + 1));
     }
-    for (uint32_t l = 0; l < L && s == LH_OK; ++l) {
+    uint64_t cnt[LH_MAX_LEVELS] = {0};
+    if (s == LH_OK && n) {
+        if (ntiles >= (1ull << 32)) s = lh_fail(ctx, LH_EOVERFLOW, "too many level tiles");
+        LevelArgs la;
+        memset(&la, 0, sizeof(la));
+        la.nlev = L;
+        for (uint32_t l = 0; l < L; ++l) {
+            la.shift[l] = shift[l];
+            la.vmask[l] = bits[l] >= 32 ? 0xFFFFFFFFu : ((1u << bits[l]) - 1u);
+            la.vals[l] = l + 1 < L ? tvals[l] : t->lv[l].vals;
+            la.offs[l] = l + 1 < L ? toffs[l] : nullptr;
+        }
+        la.runstart = runstart;
+        la.state = lstate;
+        la.ticket = ticket;
+        la.count = d_count;
+        la.status = ctx->d_status;
+        if (s == LH_OK) {
+            cudaMemsetAsync(lstate, 0, ntiles * L * sizeof(unsigned long long), ctx->stream);
+            cudaMemsetAsync(ticket, 0, sizeof(uint32_t), ctx->stream);
+            const unsigned nt = (unsigned)ntiles;
+            switch (L) {
+                case 1: LH_TRACED(ctx, "k_levels", k_levels<1><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
+                case 2: LH_TRACED(ctx, "k_levels", k_levels<2><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
+                case 3: LH_TRACED(ctx, "k_levels", k_levels<3><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
+                case 4: LH_TRACED(ctx, "k_levels", k_levels<4><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
+                case 5: LH_TRACED(ctx, "k_levels", k_levels<5><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
+                default: LH_TRACED(ctx, "k_levels", k_levels<6><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
+            }
+        }
+        STEP(lh_readback(ctx, d_count, L * sizeof(uint64_t), cnt));
+        if (s == LH_OK) {
+            uint32_t st = 0;
+            s = lh_readback(ctx, ctx->d_status, sizeof(st), &st);
+            if (s == LH_OK && st) {
+                cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream);
+                s = lh_fail(ctx, (lh_status)st, "build_trie: level offsets wait gave up");
+            }
+        }
+    }
+    for (uint32_t l = 0; l < L; ++l) t->lv[l].n = cnt[l];
+    nu = cnt[L - 1];
+    for (uint32_t l = 0; l + 1 < L && s == LH_OK; ++l) {
         TrieLevel &lv = t->lv[l];
         STEP(trie_alloc(ctx, t, &lv.vals, lv.n));
-        if (l + 1 < L) STEP(trie_alloc(ctx, t, &lv.offs, lv.n + 1));
-    }
-    for (uint32_t l = 0; l < L && s == LH_OK; ++l) {
-        uint64_t vmask = (bits[l] >= 64) ? ~0ull : ((1ull << bits[l]) - 1);
-        if (nu)
-            LH_TRACED(ctx, "k_level_emit", k_level_emit<<<G, T, 0, ctx->stream>>>(
-                ukey, nu, lflag[l], lpos[l], shift[l], vmask, t->lv[l].vals,
-                l ? lflag[l - 1] : nullptr, l ? lpos[l - 1] : nullptr, l ? t->lv[l - 1].offs : nullptr));
-        if (l + 1 < L) LH_TRACED(ctx, "k_set_u32", k_set_u32<<<1, 1, 0, ctx->stream>>>(t->lv[l].offs + t->lv[l].n, (uint32_t)t->lv[l + 1].n));
+        STEP(trie_alloc(ctx, t, &lv.offs, lv.n + 1));
+        if (s == LH_OK && lv.n) {
+            cudaError_t e = cudaMemcpyAsync(lv.vals, tvals[l], lv.n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(lv.offs, toffs[l], (lv.n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie copy: %s", cudaGetErrorString(e));
+        } else if (s == LH_OK) {
+            cudaError_t e = cudaMemsetAsync(lv.offs, 0, sizeof(uint32_t), ctx->stream);
+            if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie: %s", cudaGetErrorString(e));
+        }
     }
     // 4. annotations in leaf order
-    if (s == LH_OK && rel->nannos) {
+    if (s == LH_OK && carry) {
+        t->nannos = 1;
+        t->anno_type[0] = rel->anno_types[0];
+        if (nu == n) {
+            // no duplicates: the sorted payload is the leaf-order column
+            t->anno[0] = rid;
+            t->allocs.push_back((void *)rid);
+            t->bytes += (n ? n : 1) * sizeof(uint32_t);
+            rid = nullptr;
+        } else {
+            uint32_t *p = nullptr;
+            STEP(trie_alloc(ctx, t, &p, nu));
+            t->anno[0] = p;
+            if (s == LH_OK && nu)
+                LH_TRACED(ctx, "k_annos_carried", k_annos_carried<<<G, T, 0, ctx->stream>>>(
+                                                      rid, runstart, nu, n, merge == LH_MERGE_SUM ? 1u : 0u, p));
+        }
+    } else if (s == LH_OK && rel->nannos) {
         AnnoArgs aa;
         memset(&aa, 0, sizeof(aa));
         aa.merge = merge;
@@ -598,6 +827,7 @@ extern "C" lh_status lh_filter_trie(lh_ctx *ctx, const int32_t *col, uint64_t n,
     t->bs_min_card = pol.bs_min_card;
     const unsigned T = 256;
     const unsigned G = (unsigned)std::min<uint64_t>(lh_blocks(n, T), (uint64_t)ctx->num_sms * 16);
+    const unsigned G4 = (unsigned)std::min<uint64_t>(lh_blocks((n + 3) / 4, T), (uint64_t)ctx->num_sms * 16);
     uint32_t *flag = nullptr, *pos = nullptr;
     lh_status s = lh_alloc(ctx, &flag, n);
     if (s == LH_OK) s = lh_alloc(ctx, &pos, n + 1);

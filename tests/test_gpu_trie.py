@@ -103,6 +103,45 @@ def test_sum_merge_of_duplicate_tuples(ctx):
     tr.free()
 
 
+@pytest.mark.parametrize("dups", [True, False])
+def test_annotation_merge_paths(ctx, dups):
+    """FIRST keeps the first input row of each distinct tuple, SUM adds the
+    rows; one 4-byte column (sorted along with the keys) and the other
+    column shapes (gathered through row ids) give the same leaf order."""
+    from paper_1708_07859_b300 import lh
+    rng = np.random.default_rng(9)
+    n = 9000
+    if dups:
+        a, b = rng.integers(0, 30, n), rng.integers(0, 60, n)
+    else:
+        key = rng.permutation(70 * 200)[:n]
+        a, b = key // 200, key % 200
+    key = a.astype(np.int64) * 1000 + b
+    uk, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    u32 = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    f32 = rng.uniform(-1, 1, n).astype(np.float32)
+    f64 = rng.uniform(-1, 1, n)
+    i8 = rng.integers(-100, 100, n).astype(np.int8)
+    da, db = dev_u32(a), dev_u32(b)
+    cases = [([(u32, lh.T_U32)], lh.MERGE_FIRST), ([(f32, lh.T_F32)], lh.MERGE_FIRST),
+             ([(i8, lh.T_I8)], lh.MERGE_FIRST), ([(f32, lh.T_F32), (u32, lh.T_U32)], lh.MERGE_FIRST),
+             ([(f64, lh.T_F64)], lh.MERGE_SUM), ([(f32, lh.T_F32)], lh.MERGE_SUM)]
+    for annos, merge in cases:
+        tr = ctx.build_trie([da, db], annos=[(dev(x), ty) for x, ty in annos], merge=merge)
+        assert tr.stats().level_n[1] == uk.size
+        for c, (x, ty) in enumerate(annos):
+            got = tr.anno_array(c)
+            if merge == lh.MERGE_FIRST:
+                assert np.array_equal(got, x[first]), (ty, merge)
+            else:
+                want = np.zeros(uk.size)
+                np.add.at(want, inv, x.astype(np.float64))
+                cnt = np.bincount(inv)
+                tol = (1e-6 if ty == lh.T_F32 else 1e-13) * cnt * np.maximum(1.0, np.abs(want))
+                assert np.all(np.abs(got - want) <= tol), (ty, merge)
+        tr.free()
+
+
 def test_price_discount_expression_annotation(ctx):
     data = gen.star_schema(4000, dims=(50, 40, 30, 5), seed=11)
     from paper_1708_07859_b300 import lh
