@@ -341,13 +341,26 @@ __global__ void k_sort_hist(const uint64_t *keys, uint64_t n, int shift, uint32_
 
 // Stable scatter of one tile.  Warp w ranks the tile's keys
 // [w*512, (w+1)*512) in 16 rounds of 32 with warp-private digit counters
-// (lanes with equal digits are grouped by __match_any_sync; the group's
+// (lanes with equal digits are grouped by one ballot per digit bit; the group's
 // leader reads and advances the counter), so ranking needs no block barrier.
 // One prefix over warps and digits then turns the counters into each
 // (warp, digit) start in shared memory, where keys are placed grouped by
 // digit and written out as contiguous per-digit runs.
 constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
 constexpr int kSortWarps = kSortThreads / 32;
+
+// lanes holding the same 9-bit label (digit 0..255, or 256 for no key):
+// one ballot per label bit, keeping the lanes that agree on it
+__device__ __forceinline__ uint32_t match_label9(uint32_t d) {
+    uint32_t peers = LH_FULL;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(LH_FULL, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
 
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t n,
                                                                int shift, const uint64_t *offs, uint32_t ntiles,
@@ -379,7 +392,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
     for (int r = 0; r < kSortRounds; ++r) {
         const bool valid = wbase + (uint64_t)r * 32 + lane < n;
         const uint32_t d = valid ? (uint32_t)((kr[r] >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(LH_FULL, d);
+        const uint32_t peers = match_label9(d);
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
         if (valid && lane == leader) {
@@ -435,12 +448,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
     for (int r = 0; r < kSortRounds; ++r)
         if (wbase + (uint64_t)r * 32 + lane < n) s_vals[rk[r]] = vr[r];
     __syncthreads();
-    for (uint32_t at = t; at < tile_n; at += kSortThreads) {
-        const uint64_t k = s_keys[at];
-        const uint32_t d = (uint32_t)((k >> shift) & 255u);
-        const uint64_t dst = gbase[d] + (at - lstart[d]);
-        kout[dst] = k;
-        vout[dst] = s_vals[at];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const uint32_t at = r * kSortThreads + t;
+        if (at < tile_n) {
+            const uint64_t k = s_keys[at];
+            const uint32_t d = (uint32_t)((k >> shift) & 255u);
+            const uint64_t dst = gbase[d] + (at - lstart[d]);
+            kout[dst] = k;
+            vout[dst] = s_vals[at];
+        }
     }
 }
 
