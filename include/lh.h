@@ -100,6 +100,9 @@ typedef struct {
     double total_ms;
 } lh_trace_entry;
 lh_status lh_trace_enable(lh_ctx *ctx, int on);
+/* Restricts the events to kernels named `name` (NULL or "" = every kernel);
+ * the other kernels are still counted in launches, with total_ms 0. */
+lh_status lh_trace_only(lh_ctx *ctx, const char *name);
 lh_status lh_trace_read(lh_ctx *ctx, lh_trace_entry *out, uint32_t cap, uint32_t *n);
 lh_status lh_trace_reset(lh_ctx *ctx);
 

@@ -125,6 +125,11 @@ static cudaEvent_t pool_event(lh_ctx *ctx) {
 
 LhTraceScope::LhTraceScope(lh_ctx *c, const char *name) : ctx(c), on(c && c->trace_on) {
     if (!on) return;
+    if (!ctx->trace_only.empty() && ctx->trace_only != name) {
+        ctx->totals[name].first += 1;  // counted, not timed
+        on = false;
+        return;
+    }
     rec.name = name;
     rec.ev0 = pool_event(ctx);
     rec.ev1 = pool_event(ctx);
@@ -156,6 +161,12 @@ static void trace_fold(lh_ctx *ctx) {
 extern "C" lh_status lh_trace_enable(lh_ctx *ctx, int on) {
     if (!ctx) return LH_EINVAL;
     ctx->trace_on = on != 0;
+    return LH_OK;
+}
+
+extern "C" lh_status lh_trace_only(lh_ctx *ctx, const char *name) {
+    if (!ctx) return LH_EINVAL;
+    ctx->trace_only = name ? name : "";
     return LH_OK;
 }
 
@@ -309,45 +320,59 @@ lh_status lh_scan_u64_to_u64(lh_ctx *ctx, const uint64_t *in, uint64_t *out, uin
 }
 
 // ---------------------------------------------------------------- radix sort
-// LSD, 8-bit digits.  Per pass: per-tile digit histograms (digit-major, so
-// one exclusive scan gives every (digit, tile) its output base), then a
-// stable scatter that ranks each tile's keys in shared memory.
+// LSD, 8-bit digits, one kernel per pass.  One upfront kernel reads the keys
+// once and counts the digits of every pass (global 256-bin histograms); a
+// pass's digit d then starts at the exclusive prefix of its histogram.
+// Within a pass, tiles of 4096 keys are taken in ticket order; each tile
+// ranks its keys in shared memory, publishes its per-digit counts, and
+// finds, for every digit, the count of that digit in all earlier tiles by
+// decoupled look-back (thread d walks back over earlier tiles' states until
+// one carries an inclusive prefix).  Every tile waited on was ticketed
+// earlier, so it is already running and publishes its counts without
+// waiting.  The scatter is stable: ranks follow key order within a tile,
+// and tiles follow key order.
 
 namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 16;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per tile
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortMaxPasses = 8;
+constexpr unsigned long long kSortAgg = 1ull << 62, kSortInc = 1ull << 63, kSortVal = (1ull << 62) - 1;
+constexpr uint32_t kSortSpins = 1u << 20;
 
-__global__ void k_sort_hist(const uint64_t *keys, uint64_t n, int shift, uint32_t *hist,
-                            uint32_t ntiles) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+// digit histograms of every pass, one read of the keys
+__global__ void k_sort_upsweep(const uint64_t *keys, uint64_t n, int passes, unsigned long long *ghist) {
+    __shared__ uint32_t h[kSortMaxPasses][256];
+    for (int i = threadIdx.x; i < kSortMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
-    uint32_t d[kSortRounds];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+        uint64_t k[4];
 #pragma unroll
-    for (int r = 0; r < kSortRounds; ++r) {
-        const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
-        d[r] = i < n ? (uint32_t)((keys[i] >> shift) & 255u) : 256u;
+        for (int u = 0; u < 4; ++u) k[u] = i + u * stride < n ? keys[i + u * stride] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i + u * stride >= n) break;
+            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k[u] >> (8 * p)) & 255u], 1u);
+        }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kSortRounds; ++r)
-        if (d[r] < 256u) atomicAdd(&h[d[r]], 1u);
-    __syncthreads();
-    hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(ghist + i, (unsigned long long)c);
+    }
 }
 
-// Stable scatter of one tile.  Warp w ranks the tile's keys
-// [w*512, (w+1)*512) in 16 rounds of 32 with warp-private digit counters
-// (lanes with equal digits are grouped by one ballot per digit bit; the group's
-// leader reads and advances the counter), so ranking needs no block barrier.
-// One prefix over warps and digits then turns the counters into each
-// (warp, digit) start in shared memory, where keys are placed grouped by
-// digit and written out as contiguous per-digit runs.
-constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
-constexpr int kSortWarps = kSortThreads / 32;
+__device__ __forceinline__ void sort_store(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long sort_load(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // lanes holding the same 9-bit label (digit 0..255, or 256 for no key):
 // one ballot per label bit, keeping the lanes that agree on it
@@ -362,21 +387,38 @@ __device__ __forceinline__ uint32_t match_label9(uint32_t d) {
     return peers;
 }
 
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t n,
-                                                               int shift, const uint64_t *offs, uint32_t ntiles,
-                                                               uint64_t *kout, uint32_t *vout) {
+// One pass over one tile.  Warp w ranks the tile's keys [w*512, (w+1)*512)
+// in 16 rounds of 32 with warp-private digit counters (lanes with equal
+// digits are grouped by one ballot per digit bit; the group's leader reads
+// and advances the counter).  A prefix over warps and digits turns the
+// counters into each (warp, digit) start in shared memory, where keys are
+// placed grouped by digit and written out as contiguous per-digit runs.
+constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
+
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_onesweep(
+    const uint64_t *kin, const uint32_t *vin, uint64_t n, int shift, const unsigned long long *ghist,
+    unsigned long long *state, uint32_t *ticket, uint32_t *status, uint64_t *kout, uint32_t *vout) {
     extern __shared__ uint64_t s_keys[];                       // kSortTile keys, grouped by digit
     uint32_t *s_vals = (uint32_t *)(s_keys + kSortTile);      // their payloads
     __shared__ uint32_t wcnt[kSortWarps][256];                // per-warp digit counts, then starts
     __shared__ uint32_t lstart[256];
     __shared__ uint32_t wtot[kSortWarps];
+    __shared__ uint64_t wtot64[kSortWarps];
     __shared__ uint64_t gbase[256];
+    __shared__ uint32_t s_tile, s_ok;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
+        s_tile = atomicAdd(ticket, 1u);
+        // an earlier wait gave up: the keys no longer match the histograms
+        s_ok = *(volatile uint32_t *)status == 0;
+    }
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) wcnt[w][t] = 0;
-    gbase[t] = offs[(uint64_t)t * ntiles + blockIdx.x];
+    __syncthreads();
+    if (!s_ok) return;
+    const uint32_t tile = s_tile;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint64_t tbase = (uint64_t)blockIdx.x * kSortTile;
+    const uint64_t tbase = (uint64_t)tile * kSortTile;
     const uint32_t tile_n = (uint32_t)min((uint64_t)kSortTile, n - tbase);
     const uint64_t wbase = tbase + (uint64_t)warp * (kSortRounds * 32);
     // all of this thread's keys are loaded up front: one memory latency per tile
@@ -386,7 +428,22 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
         const uint64_t i = wbase + (uint64_t)r * 32 + lane;
         kr[r] = i < n ? kin[i] : 0;
     }
-    __syncthreads();
+    // where digit t starts in this pass's output: exclusive prefix of the histogram
+    uint64_t dstart;
+    {
+        const uint64_t c = ghist[t];
+        uint64_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t x = __shfl_up_sync(LH_FULL, incl, o);
+            if (lane >= o) incl += x;
+        }
+        if (lane == 31) wtot64[warp] = incl;
+        __syncthreads();
+        uint64_t wp = 0;
+        for (int w = 0; w < warp; ++w) wp += wtot64[w];
+        dstart = wp + incl - c;
+    }
     uint32_t rk[kSortRounds];
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
@@ -403,15 +460,18 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
         __syncwarp();
     }
     __syncthreads();
-    {
-        // thread t owns digit t: exclusive prefix over warps, then over digits
-        uint32_t c = 0;
+    // thread t owns digit t: exclusive prefix over warps and the tile's count,
+    // published at once; then each digit's run start in shared memory
+    uint32_t c = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t x = wcnt[w][t];
-            wcnt[w][t] = c;
-            c += x;
-        }
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t x = wcnt[w][t];
+        wcnt[w][t] = c;
+        c += x;
+    }
+    unsigned long long *st = state + (uint64_t)tile * 256 + t;
+    sort_store(st, (tile == 0 ? kSortInc : kSortAgg) | c);
+    {
         uint32_t incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -447,7 +507,49 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r)
         if (wbase + (uint64_t)r * 32 + lane < n) s_vals[rk[r]] = vr[r];
+    {
+        // the count of digit t in all earlier tiles, eight earlier tiles per
+        // round trip: add the published counts up to the first inclusive
+        // prefix; wait only where a count is missing
+        uint64_t excl = 0;
+        bool ok = true;
+        uint32_t spins = 0;
+        for (int64_t q = (int64_t)tile - 1; q >= 0;) {
+            unsigned long long w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[j] = q - j >= 0 ? sort_load(state + (uint64_t)(q - j) * 256 + t) : kSortInc;
+            int used = 0;
+            bool done = false, missing = false;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (done || missing) continue;
+                if ((w[j] >> 62) == 0) {
+                    missing = true;
+                    continue;
+                }
+                excl += w[j] & kSortVal;
+                ++used;
+                done = (w[j] & kSortInc) != 0;
+            }
+            if (done) break;
+            q -= used;
+            if (missing) {
+                if (++spins >= kSortSpins || ((spins & 255u) == 0 && *(volatile uint32_t *)status)) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (tile > 0) sort_store(st, kSortInc | ((excl + c) & kSortVal));
+        if (!ok) {
+            lh_set_status(status, LH_ETIMEOUT);
+            s_ok = 0;
+        }
+        gbase[t] = dstart + excl;
+    }
     __syncthreads();
+    if (!s_ok) return;
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
         const uint32_t at = r * kSortThreads + t;
@@ -455,8 +557,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
             const uint64_t k = s_keys[at];
             const uint32_t d = (uint32_t)((k >> shift) & 255u);
             const uint64_t dst = gbase[d] + (at - lstart[d]);
-            kout[dst] = k;
-            vout[dst] = s_vals[at];
+            if (dst < n) {
+                kout[dst] = k;
+                vout[dst] = s_vals[at];
+            }
         }
     }
 }
@@ -464,33 +568,38 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint64_t
 }  // namespace
 
 lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint64_t **tmp_k,
-                            uint32_t **tmp_v, uint64_t n, int bits) {
+                            uint32_t **tmp_v, uint64_t n, int bits, uint32_t *status_out) {
     if (n <= 1 || bits <= 0) return LH_OK;
-    uint64_t ntiles64 = (n + kSortTile - 1) / kSortTile;
+    const uint64_t ntiles64 = (n + kSortTile - 1) / kSortTile;
     if (ntiles64 > (1u << 24)) return lh_fail(ctx, LH_EUNSUPPORTED, "sort: too many keys");
-    uint32_t ntiles = (uint32_t)ntiles64;
-    uint32_t *hist = nullptr;
-    uint64_t *offs = nullptr;
-    LH_TRY(lh_alloc(ctx, &hist, (size_t)256 * ntiles));
-    lh_status s = lh_alloc(ctx, &offs, (size_t)256 * ntiles + 1);
-    if (s != LH_OK) {
-        lh_free(ctx, hist);
-        return s;
-    }
+    const uint32_t ntiles = (uint32_t)ntiles64;
+    const int passes = (bits + 7) / 8;
+    if (passes > kSortMaxPasses) return lh_fail(ctx, LH_EINVAL, "sort: more than 64 key bits");
+    // one zeroed block: histograms, look-back states, tickets, status
+    const size_t n_hist = (size_t)passes * 256, n_state = (size_t)passes * ntiles * 256;
+    const size_t words = n_hist + n_state + (size_t)(passes + 2) / 2 + 1;
+    unsigned long long *scratch = nullptr;
+    LH_TRY(lh_alloc(ctx, &scratch, words));
+    unsigned long long *ghist = scratch, *state = scratch + n_hist;
+    uint32_t *tickets = (uint32_t *)(state + n_state);
+    uint32_t *status = status_out ? status_out : tickets + passes;
+    lh_status s = LH_OK;
     {
-        cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
-        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort smem attribute: %s", cudaGetErrorString(e));
+        cudaError_t e = cudaMemsetAsync(scratch, 0, words * sizeof(unsigned long long), ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sort_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort setup: %s", cudaGetErrorString(e));
+    }
+    if (s == LH_OK) {
+        const unsigned g = (unsigned)std::min<uint64_t>(lh_blocks((n + 3) / 4, 256), (uint64_t)ctx->num_sms * 8);
+        LH_TRACED(ctx, "k_sort_upsweep", k_sort_upsweep<<<g, 256, 0, ctx->stream>>>(*keys, n, passes, ghist));
     }
     uint64_t *ka = *keys, *kb = *tmp_k;
     uint32_t *va = *vals, *vb = *tmp_v;
-    int passes = (bits + 7) / 8;
     for (int p = 0; p < passes && s == LH_OK; ++p) {
-        int shift = 8 * p;
-        LH_TRACED(ctx, "k_sort_hist", k_sort_hist<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, n, shift, hist, ntiles));
-        s = lh_scan_u32_to_u64(ctx, hist, offs, (uint64_t)256 * ntiles);
-        if (s != LH_OK) break;
-        LH_TRACED(ctx, "k_sort_scatter", k_sort_scatter<<<ntiles, kSortThreads, kScatterSmem, ctx->stream>>>(
-                                             ka, va, n, shift, offs, ntiles, kb, vb));
+        LH_TRACED(ctx, "k_sort_onesweep", k_sort_onesweep<<<ntiles, kSortThreads, kScatterSmem, ctx->stream>>>(
+                                              ka, va, n, 8 * p, ghist + (size_t)p * 256,
+                                              state + (size_t)p * ntiles * 256, tickets + p, status, kb, vb));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort: %s", cudaGetErrorString(e));
         uint64_t *tk = ka; ka = kb; kb = tk;
@@ -501,7 +610,11 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint6
     *tmp_k = kb;
     *vals = va;
     *tmp_v = vb;
-    lh_free(ctx, hist);
-    lh_free(ctx, offs);
+    if (s == LH_OK && !status_out) {
+        uint32_t st = 0;
+        s = lh_readback(ctx, status, sizeof(st), &st);
+        if (s == LH_OK && st) s = lh_fail(ctx, (lh_status)st, "sort: look-back wait gave up");
+    }
+    lh_free(ctx, scratch);
     return s;
 }

@@ -36,6 +36,7 @@ struct lh_ctx {
     static constexpr int kPinnedWords = 64;
     // kernel tracing: CUDA events recorded on the launching stream around launches
     bool trace_on = false;
+    std::string trace_only;         // when set, events bracket only this kernel
     std::vector<cudaEvent_t> ev_pool;
     std::vector<lh_trace_rec> pending;
     std::map<std::string, std::pair<uint64_t, double>> totals;
@@ -113,9 +114,11 @@ lh_status lh_scan_u64_to_u64(lh_ctx *ctx, const uint64_t *in, uint64_t *out, uin
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.
 // (*keys, *vals) hold the input and (*tmp_k, *tmp_v) scratch of length n; on
 // return the pointers are swapped as needed so that (*keys, *vals) hold the
-// sorted pairs and (*tmp_k, *tmp_v) the scratch.
+// sorted pairs and (*tmp_k, *tmp_v) the scratch.  status: a zeroed device
+// word that receives LH_ETIMEOUT if a bounded wait gives up (the caller
+// reads it back), or null for the sort to read its own back.
 lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint64_t **tmp_k,
-                            uint32_t **tmp_v, uint64_t n, int bits);
+                            uint32_t **tmp_v, uint64_t n, int bits, uint32_t *status);
 
 // ----------------------------------------------------------------------- tries
 

@@ -421,6 +421,20 @@ __global__ void __launch_bounds__(256) k_layout_bits(const uint32_t *vals, const
     }
 }
 
+struct LayoutTotals {
+    const uint32_t *nbs[LH_MAX_LEVELS];  // bitset sets of level l (end of its slot scan), or null
+    const uint64_t *nw[LH_MAX_LEVELS];   // bitset words of level l (end of its word scan), or null
+    uint32_t nlev;
+};
+
+__global__ void k_layout_totals(LayoutTotals a, uint64_t *out) {
+    const uint32_t l = threadIdx.x;
+    if (l < LH_MAX_LEVELS) {
+        out[2 * l] = (l < a.nlev && a.nbs[l]) ? *a.nbs[l] : 0;
+        out[2 * l + 1] = (l < a.nlev && a.nw[l]) ? *a.nw[l] : 0;
+    }
+}
+
 __global__ void k_popc_words(const uint32_t *words, uint64_t n, uint32_t *pc) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
@@ -485,6 +499,11 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
             lh_free(ctx, slot_set[l]);
         }
     };
+    // every level decides and counts first; one readback brings all totals
+    LayoutTotals lt;
+    memset(&lt, 0, sizeof(lt));
+    lt.nlev = t->nlevels;
+    bool any = false;
     for (uint32_t l = 0; l < t->nlevels && s == LH_OK; ++l) {
         TrieLevel &L = t->lv[l];
         L.nsets = (l == 0) ? 1 : t->lv[l - 1].n;
@@ -500,13 +519,24 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
             L.vals, poffs, L.nsets, n0, t->bs_ratio, t->bs_min_card, tmp_isbs[l], tmp_words[l]));
         if ((s = lh_scan_u32_to_u32(ctx, tmp_isbs[l], tmp_slot[l], L.nsets)) != LH_OK) break;
         if ((s = lh_scan_u64_to_u64(ctx, tmp_words[l], tmp_woff[l], L.nsets)) != LH_OK) break;
-        uint32_t nbs = 0;
-        uint64_t nw = 0;
-        if ((s = lh_readback(ctx, tmp_slot[l] + L.nsets, sizeof(uint32_t), &nbs)) != LH_OK) break;
-        if ((s = lh_readback(ctx, tmp_woff[l] + L.nsets, sizeof(uint64_t), &nw)) != LH_OK) break;
-        L.n_bs = nbs;
-        level_word_base[l] = total_words;
-        total_words += nw;
+        lt.nbs[l] = tmp_slot[l] + L.nsets;
+        lt.nw[l] = tmp_woff[l] + L.nsets;
+        any = true;
+    }
+    if (s == LH_OK && any) {
+        uint64_t *d_tot = nullptr;
+        uint64_t h_tot[2 * LH_MAX_LEVELS] = {0};
+        s = lh_alloc(ctx, &d_tot, 2 * LH_MAX_LEVELS);
+        if (s == LH_OK) {
+            LH_TRACED(ctx, "k_layout_totals", k_layout_totals<<<1, 32, 0, ctx->stream>>>(lt, d_tot));
+            s = lh_readback(ctx, d_tot, sizeof(h_tot), h_tot);
+        }
+        lh_free(ctx, d_tot);
+        for (uint32_t l = 0; l < t->nlevels && s == LH_OK; ++l) {
+            t->lv[l].n_bs = h_tot[2 * l];
+            level_word_base[l] = total_words;
+            total_words += h_tot[2 * l + 1];
+        }
     }
     // ranks are 32-bit: the arena's bit count must stay below 2^32
     if (s == LH_OK && total_words >= (1ull << 27))
@@ -537,10 +567,11 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
         LH_TRACED(ctx, "k_layout_chunks", k_layout_chunks<<<lh_blocks(L.n_bs, T, 1 << 16), T, 0, ctx->stream>>>(
             L.bs_meta, L.n_bs, chunks));
         s = lh_scan_u32_to_u32(ctx, chunks, coff, L.n_bs);
-        uint32_t nch = 0;
-        if (s == LH_OK) s = lh_readback(ctx, coff + L.n_bs, sizeof(uint32_t), &nch);
-        if (s == LH_OK && nch)
-            LH_TRACED(ctx, "k_layout_bits", k_layout_bits<<<std::min<uint32_t>(nch, (uint32_t)ctx->num_sms * 16), 256, 0, ctx->stream>>>(
+        // the kernel reads its chunk count on the device; the grid only needs
+        // a bound (every set has at least one chunk)
+        const uint64_t max_chunks = (uint64_t)L.n_bs + (L.n + kBitsChunk - 1) / kBitsChunk;
+        if (s == LH_OK)
+            LH_TRACED(ctx, "k_layout_bits", k_layout_bits<<<(unsigned)std::min<uint64_t>(max_chunks, (uint64_t)ctx->num_sms * 16), 256, 0, ctx->stream>>>(
                 L.vals, poffs, n0, L.bs_meta, slot_set[l], coff, (uint32_t)L.n_bs, t->words));
         lh_free(ctx, chunks);
         lh_free(ctx, coff);
@@ -662,23 +693,28 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     STEP(lh_alloc(ctx, &tkey, n));
     STEP(lh_alloc(ctx, &rid, n));
     STEP(lh_alloc(ctx, &trid, n));
+    // level counts, then one status word (sort and level waits) read back together
+    STEP(lh_alloc(ctx, &d_count, L + 1));
+    if (s == LH_OK) {
+        cudaError_t e = cudaMemsetAsync(d_count, 0, (L + 1) * sizeof(uint64_t), ctx->stream);
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie: %s", cudaGetErrorString(e));
+    }
     if (s == LH_OK && n) {
         LH_TRACED(ctx, "k_pack", k_pack<<<G4, T, 0, ctx->stream>>>(pa, n, key, rid));
-        STEP(lh_radix_sort_u64(ctx, &key, &rid, &tkey, &trid, n, (int)total_bits));
+        STEP(lh_radix_sort_u64(ctx, &key, &rid, &tkey, &trid, n, (int)total_bits, (uint32_t *)(d_count + L)));
     }
     // 3. levels: the leaf level is written in place (capacity n), the levels
     //    above into temporaries, copied out once their sizes are known
     const uint64_t ntiles = (n + kLvTile - 1) / kLvTile;
     STEP(trie_alloc(ctx, t, &t->lv[L - 1].vals, n));
     STEP(lh_alloc(ctx, &runstart, n));
-    STEP(lh_alloc(ctx, &d_count, L));
     STEP(lh_alloc(ctx, &ticket, 1));
     STEP(lh_alloc(ctx, &lstate, ntiles * L));
     for (uint32_t l = 0; l + 1 < L; ++l) {
         STEP(lh_alloc(ctx, &tvals[l], n));
         STEP(lh_alloc(ctx, &toffs[l], n + 1));
     }
-    uint64_t cnt[LH_MAX_LEVELS] = {0};
+    uint64_t cnt[LH_MAX_LEVELS + 1] = {0};
     if (s == LH_OK && n) {
         if (ntiles >= (1ull << 32)) s = lh_fail(ctx, LH_EOVERFLOW, "too many level tiles");
         LevelArgs la;
@@ -694,7 +730,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         la.state = lstate;
         la.ticket = ticket;
         la.count = d_count;
-        la.status = ctx->d_status;
+        la.status = (uint32_t *)(d_count + L);
         if (s == LH_OK) {
             cudaMemsetAsync(lstate, 0, ntiles * L * sizeof(unsigned long long), ctx->stream);
             cudaMemsetAsync(ticket, 0, sizeof(uint32_t), ctx->stream);
@@ -708,15 +744,9 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
                 default: LH_TRACED(ctx, "k_levels", k_levels<6><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
             }
         }
-        STEP(lh_readback(ctx, d_count, L * sizeof(uint64_t), cnt));
-        if (s == LH_OK) {
-            uint32_t st = 0;
-            s = lh_readback(ctx, ctx->d_status, sizeof(st), &st);
-            if (s == LH_OK && st) {
-                cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream);
-                s = lh_fail(ctx, (lh_status)st, "build_trie: level offsets wait gave up");
-            }
-        }
+        STEP(lh_readback(ctx, d_count, (L + 1) * sizeof(uint64_t), cnt));
+        if (s == LH_OK && (uint32_t)cnt[L])
+            s = lh_fail(ctx, (lh_status)(uint32_t)cnt[L], "build_trie: a bounded wait (sort or level offsets) gave up");
     }
     for (uint32_t l = 0; l < L; ++l) t->lv[l].n = cnt[l];
     nu = cnt[L - 1];

@@ -132,6 +132,7 @@ EXPORTS = {
     "lh_copy_h2d": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
     "lh_selftest_bounded_wait": [C.c_void_p, C.c_uint32],
     "lh_trace_enable": [C.c_void_p, C.c_int],
+    "lh_trace_only": [C.c_void_p, C.c_char_p],
     "lh_trace_read": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
     "lh_trace_reset": [C.c_void_p],
     "lh_build_trie": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
@@ -235,6 +236,10 @@ class Context:
 
     def trace(self, on=True):
         self._check(lib().lh_trace_enable(self.h, 1 if on else 0))
+
+    def trace_only(self, name=None):
+        """Time only kernels called `name` (None: every kernel); all are counted."""
+        self._check(lib().lh_trace_only(self.h, name.encode() if name else None))
 
     def trace_reset(self):
         self._check(lib().lh_trace_reset(self.h))
