@@ -71,6 +71,11 @@ typedef struct lh_batch lh_batch;
 lh_status lh_create(lh_ctx **out, void *cuda_stream);
 lh_status lh_destroy(lh_ctx *ctx);
 lh_status lh_set_stream(lh_ctx *ctx, void *cuda_stream);
+/* Maps `bytes` of device memory into the context's pool up front (one
+ * allocation, freed at once and kept), so that later temporaries of varying
+ * sizes are carved from one mapping instead of growing the pool call by
+ * call.  Blocks until done; LH_ENOMEM if the device cannot provide it. */
+lh_status lh_pool_reserve(lh_ctx *ctx, uint64_t bytes);
 /* Last error message of this context (never NULL). */
 const char *lh_last_error(const lh_ctx *ctx);
 /* Wait for the stream; return the first device-side error word, if any. */

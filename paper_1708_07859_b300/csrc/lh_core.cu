@@ -72,6 +72,21 @@ extern "C" lh_status lh_destroy(lh_ctx *ctx) {
     return LH_OK;
 }
 
+extern "C" lh_status lh_pool_reserve(lh_ctx *ctx, uint64_t bytes) {
+    if (!ctx || !ctx->pool) return LH_EINVAL;
+    if (bytes == 0) return LH_OK;
+    void *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, ctx->pool, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return lh_fail(ctx, LH_ENOMEM, "pool reserve of %llu bytes: %s", (unsigned long long)bytes,
+                       cudaGetErrorString(e));
+    }
+    LH_CU(cudaFreeAsync(p, ctx->stream));
+    LH_CU(cudaStreamSynchronize(ctx->stream));
+    return LH_OK;
+}
+
 extern "C" lh_status lh_set_stream(lh_ctx *ctx, void *stream) {
     if (!ctx) return LH_EINVAL;
     ctx->stream = (cudaStream_t)stream;

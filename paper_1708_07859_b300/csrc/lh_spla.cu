@@ -79,13 +79,12 @@ __global__ void k_spgemm_bound(DTrie A, DTrie B, uint32_t nA0, uint32_t *ub) {
 // Global hash capacity for rows above the shared bound (0 for the others),
 // and the number of rows the sort-based kernel does not take (more than
 // 256 products or more than 32 A entries).
-// sizes[0..2] = (U, G, hash rows); the hash-row counter is sizes[0] on entry
-__global__ void k_spgemm_sizes(const uint64_t *u_end, const uint64_t *g_end, unsigned long long *sizes) {
+// sizes[0..1] = (U, hash rows); the hash-row counter is sizes[0] on entry
+__global__ void k_spgemm_sizes(const uint64_t *u_end, unsigned long long *sizes) {
     if (threadIdx.x == 0) {
         const unsigned long long h = sizes[0];
         sizes[0] = *u_end;
-        sizes[1] = *g_end;
-        sizes[2] = h;
+        sizes[1] = h;
     }
 }
 
@@ -590,22 +589,25 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
     STEP(lh_alloc(ctx, &tmp_off, (size_t)n0 + 1));
     STEP(lh_alloc(ctx, &gcap, n0));
     STEP(lh_alloc(ctx, &goff, (size_t)n0 + 1));
-    STEP(lh_alloc(ctx, &n_hash, 3));
+    STEP(lh_alloc(ctx, &n_hash, 2));
     if (s == LH_OK && n0) {
         LH_TRACED(ctx, "k_spgemm_bound", k_spgemm_bound<<<grid, T, 0, ctx->stream>>>(A, B, n0, ub));
         cudaMemsetAsync(n_hash, 0, sizeof(unsigned long long), ctx->stream);
         LH_TRACED(ctx, "k_spgemm_gcap", k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(ub, a->lv[0].offs, n0, gcap, n_hash));
     }
     STEP(lh_scan_u32_to_u64(ctx, ub, tmp_off, n0));
-    STEP(lh_scan_u64_to_u64(ctx, gcap, goff, n0));
     if (s == LH_OK && n0) {
-        // the three sizes the host allocates by, in one readback
-        LH_TRACED(ctx, "k_spgemm_sizes", k_spgemm_sizes<<<1, 32, 0, ctx->stream>>>(tmp_off + n0, goff + n0, n_hash));
-        uint64_t h[3] = {0, 0, 0};
+        // U and the hash-row count in one readback
+        LH_TRACED(ctx, "k_spgemm_sizes", k_spgemm_sizes<<<1, 32, 0, ctx->stream>>>(tmp_off + n0, n_hash));
+        uint64_t h[2] = {0, 0};
         STEP(lh_readback(ctx, n_hash, sizeof(h), h));
         U = h[0];
-        G = h[1];
-        hash_rows = h[2];
+        hash_rows = h[1];
+    }
+    if (s == LH_OK && hash_rows) {
+        // global hash tables only for rows whose products overflow shared memory
+        STEP(lh_scan_u64_to_u64(ctx, gcap, goff, n0));
+        STEP(lh_readback(ctx, goff + n0, sizeof(uint64_t), &G));
     }
     STEP(lh_alloc(ctx, &tcol, U));
     STEP(lh_alloc(ctx, &tval, U));

@@ -329,9 +329,11 @@ size_t dtype_size(uint32_t t) {
 // --- layout ---------------------------------------------------------------
 
 // Per set: decide bitset and its word count (0 = uint layout).
+// tot[0] += bitset sets of the level, tot[1] += their words
 __global__ void k_layout_decide(const uint32_t *vals, const uint32_t *poffs, uint64_t nsets,
                                 uint32_t n0, uint32_t ratio, uint32_t min_card, uint32_t *is_bs,
-                                uint64_t *nwords) {
+                                uint64_t *nwords, unsigned long long *tot) {
+    unsigned long long my_bs = 0, my_w = 0;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsets;
          s += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t lo = poffs ? poffs[s] : 0, hi = poffs ? poffs[s + 1] : n0;
@@ -350,6 +352,17 @@ __global__ void k_layout_decide(const uint32_t *vals, const uint32_t *poffs, uin
         }
         is_bs[s] = bs;
         nwords[s] = w;
+        my_bs += bs;
+        my_w += w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_bs += __shfl_xor_sync(LH_FULL, my_bs, o);
+        my_w += __shfl_xor_sync(LH_FULL, my_w, o);
+    }
+    if ((threadIdx.x & 31) == 0 && my_bs) {
+        atomicAdd(tot, my_bs);
+        atomicAdd(tot + 1, my_w);
     }
 }
 
@@ -421,20 +434,6 @@ __global__ void __launch_bounds__(256) k_layout_bits(const uint32_t *vals, const
     }
 }
 
-struct LayoutTotals {
-    const uint32_t *nbs[LH_MAX_LEVELS];  // bitset sets of level l (end of its slot scan), or null
-    const uint64_t *nw[LH_MAX_LEVELS];   // bitset words of level l (end of its word scan), or null
-    uint32_t nlev;
-};
-
-__global__ void k_layout_totals(LayoutTotals a, uint64_t *out) {
-    const uint32_t l = threadIdx.x;
-    if (l < LH_MAX_LEVELS) {
-        out[2 * l] = (l < a.nlev && a.nbs[l]) ? *a.nbs[l] : 0;
-        out[2 * l + 1] = (l < a.nlev && a.nw[l]) ? *a.nw[l] : 0;
-    }
-}
-
 __global__ void k_popc_words(const uint32_t *words, uint64_t n, uint32_t *pc) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
@@ -499,44 +498,46 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
             lh_free(ctx, slot_set[l]);
         }
     };
-    // every level decides and counts first; one readback brings all totals
-    LayoutTotals lt;
-    memset(&lt, 0, sizeof(lt));
-    lt.nlev = t->nlevels;
+    // every level decides and counts its bitset sets and words on the device;
+    // one readback brings all totals, and only levels with bitset sets go on
+    unsigned long long *d_tot = nullptr;
+    unsigned long long h_tot[2 * LH_MAX_LEVELS] = {0};
     bool any = false;
-    for (uint32_t l = 0; l < t->nlevels && s == LH_OK; ++l) {
+    for (uint32_t l = 0; l < t->nlevels; ++l) {
         TrieLevel &L = t->lv[l];
         L.nsets = (l == 0) ? 1 : t->lv[l - 1].n;
         L.n_bs = 0;
-        if (t->bs_ratio == 0 || L.n == 0) continue;
-        const uint32_t *poffs = (l == 0) ? nullptr : t->lv[l - 1].offs;
-        uint32_t n0 = (uint32_t)L.n;
-        if ((s = lh_alloc(ctx, &tmp_isbs[l], L.nsets)) != LH_OK) break;
-        if ((s = lh_alloc(ctx, &tmp_slot[l], L.nsets + 1)) != LH_OK) break;
-        if ((s = lh_alloc(ctx, &tmp_words[l], L.nsets)) != LH_OK) break;
-        if ((s = lh_alloc(ctx, &tmp_woff[l], L.nsets + 1)) != LH_OK) break;
-        LH_TRACED(ctx, "k_layout_decide", k_layout_decide<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
-            L.vals, poffs, L.nsets, n0, t->bs_ratio, t->bs_min_card, tmp_isbs[l], tmp_words[l]));
-        if ((s = lh_scan_u32_to_u32(ctx, tmp_isbs[l], tmp_slot[l], L.nsets)) != LH_OK) break;
-        if ((s = lh_scan_u64_to_u64(ctx, tmp_words[l], tmp_woff[l], L.nsets)) != LH_OK) break;
-        lt.nbs[l] = tmp_slot[l] + L.nsets;
-        lt.nw[l] = tmp_woff[l] + L.nsets;
-        any = true;
+        any = any || (t->bs_ratio != 0 && L.n != 0);
     }
-    if (s == LH_OK && any) {
-        uint64_t *d_tot = nullptr;
-        uint64_t h_tot[2 * LH_MAX_LEVELS] = {0};
+    if (any) {
         s = lh_alloc(ctx, &d_tot, 2 * LH_MAX_LEVELS);
         if (s == LH_OK) {
-            LH_TRACED(ctx, "k_layout_totals", k_layout_totals<<<1, 32, 0, ctx->stream>>>(lt, d_tot));
-            s = lh_readback(ctx, d_tot, sizeof(h_tot), h_tot);
+            cudaError_t e = cudaMemsetAsync(d_tot, 0, 2 * LH_MAX_LEVELS * sizeof(unsigned long long), ctx->stream);
+            if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "layout: %s", cudaGetErrorString(e));
         }
-        lh_free(ctx, d_tot);
-        for (uint32_t l = 0; l < t->nlevels && s == LH_OK; ++l) {
-            t->lv[l].n_bs = h_tot[2 * l];
-            level_word_base[l] = total_words;
-            total_words += h_tot[2 * l + 1];
-        }
+    }
+    for (uint32_t l = 0; l < t->nlevels && s == LH_OK && any; ++l) {
+        TrieLevel &L = t->lv[l];
+        if (t->bs_ratio == 0 || L.n == 0) continue;
+        const uint32_t *poffs = (l == 0) ? nullptr : t->lv[l - 1].offs;
+        if ((s = lh_alloc(ctx, &tmp_isbs[l], L.nsets)) != LH_OK) break;
+        if ((s = lh_alloc(ctx, &tmp_words[l], L.nsets)) != LH_OK) break;
+        LH_TRACED(ctx, "k_layout_decide", k_layout_decide<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
+            L.vals, poffs, L.nsets, (uint32_t)L.n, t->bs_ratio, t->bs_min_card, tmp_isbs[l], tmp_words[l], d_tot + 2 * l));
+    }
+    if (s == LH_OK && any) s = lh_readback(ctx, d_tot, sizeof(h_tot), h_tot);
+    lh_free(ctx, d_tot);
+    for (uint32_t l = 0; l < t->nlevels && s == LH_OK; ++l) {
+        TrieLevel &L = t->lv[l];
+        L.n_bs = h_tot[2 * l];
+        level_word_base[l] = total_words;
+        total_words += h_tot[2 * l + 1];
+        if (L.n_bs == 0) continue;
+        // each bitset set's slot and first word: exclusive scans over the sets
+        if ((s = lh_alloc(ctx, &tmp_slot[l], L.nsets + 1)) != LH_OK) break;
+        if ((s = lh_alloc(ctx, &tmp_woff[l], L.nsets + 1)) != LH_OK) break;
+        if ((s = lh_scan_u32_to_u32(ctx, tmp_isbs[l], tmp_slot[l], L.nsets)) != LH_OK) break;
+        if ((s = lh_scan_u64_to_u64(ctx, tmp_words[l], tmp_woff[l], L.nsets)) != LH_OK) break;
     }
     // ranks are 32-bit: the arena's bit count must stay below 2^32
     if (s == LH_OK && total_words >= (1ull << 27))

@@ -131,6 +131,7 @@ EXPORTS = {
     "lh_copy_d2h": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
     "lh_copy_h2d": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
     "lh_selftest_bounded_wait": [C.c_void_p, C.c_uint32],
+    "lh_pool_reserve": [C.c_void_p, C.c_uint64],
     "lh_trace_enable": [C.c_void_p, C.c_int],
     "lh_trace_only": [C.c_void_p, C.c_char_p],
     "lh_trace_read": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
@@ -236,6 +237,10 @@ class Context:
 
     def trace(self, on=True):
         self._check(lib().lh_trace_enable(self.h, 1 if on else 0))
+
+    def pool_reserve(self, nbytes):
+        """Map `nbytes` into the context's memory pool up front (lh_pool_reserve)."""
+        self._check(lib().lh_pool_reserve(self.h, int(nbytes)))
 
     def trace_only(self, name=None):
         """Time only kernels called `name` (None: every kernel); all are counted."""

@@ -44,3 +44,18 @@ def test_bad_arguments_are_refused(ctx, lhlib):
     with pytest.raises(lh.LHError):
         ctx.build_trie([dev_u32(s), dev_u32(d)], key_order=[0, 0])
     t.free()
+
+
+def test_pool_reserve_and_refusal(ctx, orc, lhlib):
+    """A reservation maps memory into the context's pool; one the device
+    cannot provide is refused with LH_ENOMEM (an allocation error, not a
+    fault) and the context goes on working."""
+    lh = lhlib
+    ctx.pool_reserve(64 << 20)
+    with pytest.raises(lh.LHError) as e:
+        ctx.pool_reserve(1 << 50)
+    assert e.value.status == lh.ENOMEM
+    s, d = gen.gnm_edges(300, 2000, 4)
+    g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), "triangle")
+    assert g.run(lh.make_plan([0, 1, 2]))[0] == orc.triangle_count(s, d)
+    g.free()
