@@ -132,8 +132,9 @@ class Step:
 
     def run(self, keep=False):
         lh, ctx, d = self.lh, self.ctx, self.d
-        ta = lh.matrix_trie(ctx, d["Ar"], d["Ac"], d["Av"])
-        tb = lh.matrix_trie(ctx, d["Br"], d["Bc"], d["Bv"])
+        dims = (self.n, self.n)    # the matrices' shapes declare the key domains
+        ta = lh.matrix_trie(ctx, d["Ar"], d["Ac"], d["Av"], dims=dims)
+        tb = lh.matrix_trie(ctx, d["Br"], d["Bc"], d["Bv"], dims=dims)
         q1 = lh.spmv_query(self.n, d["x"], int(d["Ar"].numel()))
         p1 = ctx.plan(q1)
         r1 = ctx.join_aggregate(q1, p1, [ta])

@@ -123,6 +123,11 @@ typedef struct {
     uint32_t nannos;
     const void *annos[LH_MAX_ANNOS];
     uint32_t anno_types[LH_MAX_ANNOS]; /* lh_dtype */
+    /* Optional domain size of each key column: every value is < key_bound[c]
+     * (a matrix's dimensions, a dimension table's cardinality); 0 = unknown.
+     * When every key column has one, the build takes its bit widths from
+     * them instead of reading the columns' maxima back. */
+    uint32_t key_bound[LH_MAX_LEVELS];
 } lh_relation_desc;
 
 /* How annotations of duplicate key tuples merge (every tuple has one
@@ -151,10 +156,13 @@ typedef struct {
  * (key_order: host array, a permutation of [0, nkeys)).  Radix-sorts the
  * packed key tuples (total key bits <= 64), removes duplicates merging their
  * annotations per `merge`, emits CSR levels, decides each set's layout and
- * gathers annotations into leaf order.  Synchronises once (to size levels).
- * Errors: LH_EINVAL (bad order, nkeys 0 or > LH_MAX_LEVELS, merge/type
- * mismatch), LH_EUNSUPPORTED (> 64 packed key bits), LH_EOVERFLOW (a level
- * larger than 2^32 - 1 entries), LH_ENOMEM. */
+ * gathers annotations into leaf order.  Synchronises to size the levels and
+ * the bitset arena, and once more to read the key maxima unless every key
+ * column has a key_bound.  Errors: LH_EINVAL (bad order, nkeys 0 or >
+ * LH_MAX_LEVELS, merge/type mismatch, a key value at or above its declared
+ * key_bound), LH_EUNSUPPORTED (> 64 packed key bits), LH_EOVERFLOW (a level
+ * larger than 2^32 - 1 entries), LH_ETIMEOUT (a bounded device wait gave up),
+ * LH_ENOMEM. */
 lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel, const uint32_t *key_order,
                         const lh_layout_policy *layout, lh_merge merge, lh_trie **out);
 
@@ -343,7 +351,9 @@ lh_status lh_edge_key_order(const lh_query *q, const lh_plan_t *plan, uint32_t e
  * lh_result_free.  GENERIC: count / sum totals and, with GROUP BY, the dense
  * per-group arrays (group g = g0 * card1 + g1).  SPMV: y (fp32, nrows).
  * SPGEMM: CSR C over the nrows distinct rows of A (c_row: their ids,
- * c_off: nrows+1 uint64, c_col uint32 ascending per row, c_val fp32). */
+ * c_off: nrows+1 uint64, c_col uint32 ascending per row, c_val fp32).  The
+ * first nnz entries of c_col / c_val hold C; their allocation is the product
+ * bound sum_i sum_{k in A_i} |B_k|, so the join needs no readback of nnz. */
 typedef struct {
     uint32_t exec;
     uint64_t count;

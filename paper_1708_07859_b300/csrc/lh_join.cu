@@ -623,6 +623,10 @@ extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v
     v->group_count = r->d_gcount;
     v->nrows = r->nrows;
     v->y = r->y;
+    if (r->nnz_pending) {
+        LH_CU(cudaMemcpy(&r->nnz, r->c_off + r->nrows, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        r->nnz_pending = false;
+    }
     v->nnz = r->nnz;
     v->c_row = r->c_row;
     v->c_off = r->c_off;

@@ -13,6 +13,7 @@ struct lh_result {
     uint64_t nrows = 0;
     float *y = nullptr;
     uint64_t nnz = 0;
+    bool nnz_pending = false;  // SPGEMM: nnz = c_off[nrows], read at lh_result_wait
     const uint32_t *c_row = nullptr;
     uint64_t *c_off = nullptr;
     uint32_t *c_col = nullptr;

@@ -580,7 +580,7 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
     unsigned long long hash_rows = 0;
     float *ghi = nullptr, *glo = nullptr, *tval = nullptr;
     lh_status s = LH_OK;
-    uint64_t U = 0, G = 0, nnz = 0;
+    uint64_t U = 0, G = 0;
     const unsigned T = 256;
     const unsigned grid = (unsigned)std::min<uint64_t>(lh_blocks(n0, T), (uint64_t)ctx->num_sms * 8);
 #define STEP(x) if (s == LH_OK) s = (x)
@@ -638,12 +638,11 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "spgemm: %s", cudaGetErrorString(e));
     }
     STEP(lh_scan_u32_to_u64(ctx, cnt, r->c_off, n0));
-    STEP(lh_readback(ctx, r->c_off + n0, sizeof(uint64_t), &nnz));
-    if (s == LH_OK) {
-        r->nnz = nnz;
-        s = res_alloc(ctx, r, &r->c_col, nnz);
-        STEP(res_alloc(ctx, r, &r->c_val, nnz));
-    }
+    // C is allocated at the product bound U, so no readback is needed here:
+    // nnz = c_off[nrows] is read when the result is waited on
+    STEP(res_alloc(ctx, r, &r->c_col, std::max<uint64_t>(U, 1)));
+    STEP(res_alloc(ctx, r, &r->c_val, std::max<uint64_t>(U, 1)));
+    if (s == LH_OK) r->nnz_pending = true;
     if (s == LH_OK && n0)
         LH_TRACED(ctx, "k_spgemm_gather", k_spgemm_gather<<<grid, T, 0, ctx->stream>>>(n0, tmp_off, r->c_off, tcol, tval, r->c_col, r->c_val));
 #undef STEP

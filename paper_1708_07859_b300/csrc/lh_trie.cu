@@ -10,8 +10,10 @@ namespace {
 struct PackArgs {
     const uint32_t *col[LH_MAX_LEVELS];
     uint32_t shift[LH_MAX_LEVELS];
+    uint32_t bound[LH_MAX_LEVELS];  // declared domain sizes checked while packing, 0 = none
     uint32_t nlev;
     const uint32_t *payload;  // 4-byte annotation carried through the sort, or null: row ids
+    uint32_t *status;         // LH_EINVAL when a value breaks its bound
 };
 
 // Largest value of every key column, one launch: each thread takes four
@@ -47,13 +49,19 @@ __global__ void k_pack(PackArgs a, uint64_t n, uint64_t *key, uint32_t *rid) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
         uint64_t k[4] = {0, 0, 0, 0};
         uint32_t r[4];
+        bool bad = false;
 #pragma unroll
         for (int l = 0; l < LH_MAX_LEVELS; ++l) {
             if (l >= (int)a.nlev) break;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (i + u * stride < n) k[u] |= (uint64_t)a.col[l][i + u * stride] << a.shift[l];
+                if (i + u * stride < n) {
+                    const uint32_t v = a.col[l][i + u * stride];
+                    bad |= a.bound[l] != 0 && v >= a.bound[l];
+                    k[u] |= (uint64_t)v << a.shift[l];
+                }
         }
+        if (bad) lh_set_status(a.status, LH_EINVAL);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             r[u] = i + u * stride < n ? (a.payload ? a.payload[i + u * stride] : (uint32_t)(i + u * stride)) : 0u;
@@ -330,9 +338,13 @@ size_t dtype_size(uint32_t t) {
 
 // Per set: decide bitset and its word count (0 = uint layout).
 // tot[0] += bitset sets of the level, tot[1] += their words
+// The level's set count and entry count come from the host (nsets, n0) or,
+// when the pointers are given, from the device (the level build's counts).
 __global__ void k_layout_decide(const uint32_t *vals, const uint32_t *poffs, uint64_t nsets,
-                                uint32_t n0, uint32_t ratio, uint32_t min_card, uint32_t *is_bs,
-                                uint64_t *nwords, unsigned long long *tot) {
+                                uint32_t n0, const uint64_t *d_nsets, const uint64_t *d_n0, uint32_t ratio,
+                                uint32_t min_card, uint32_t *is_bs, uint64_t *nwords, unsigned long long *tot) {
+    if (d_nsets) nsets = *d_nsets;
+    if (d_n0) n0 = (uint32_t)*d_n0;
     unsigned long long my_bs = 0, my_w = 0;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsets;
          s += (uint64_t)gridDim.x * blockDim.x) {
@@ -481,7 +493,19 @@ DTrie lh_trie_dview(const lh_trie *t) {
     return d;
 }
 
-lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
+// Layout decisions already taken on the device together with the level
+// build (arrays owned by the layout from then on) and their totals.
+struct LayoutPre {
+    uint32_t *isbs[LH_MAX_LEVELS];
+    uint64_t *words[LH_MAX_LEVELS];
+    unsigned long long tot[2 * LH_MAX_LEVELS];
+};
+
+static lh_status trie_layout(lh_ctx *ctx, lh_trie *t, LayoutPre *pre);
+
+lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) { return trie_layout(ctx, t, nullptr); }
+
+static lh_status trie_layout(lh_ctx *ctx, lh_trie *t, LayoutPre *pre) {
     const unsigned T = 256;
     uint64_t total_words = 0;
     uint64_t level_word_base[LH_MAX_LEVELS] = {0};
@@ -509,6 +533,16 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
         L.n_bs = 0;
         any = any || (t->bs_ratio != 0 && L.n != 0);
     }
+    if (pre) {
+        for (uint32_t l = 0; l < t->nlevels; ++l) {
+            tmp_isbs[l] = pre->isbs[l];
+            tmp_words[l] = pre->words[l];
+            pre->isbs[l] = nullptr;
+            pre->words[l] = nullptr;
+        }
+        memcpy(h_tot, pre->tot, sizeof(h_tot));
+        any = false;  // decided and counted already
+    }
     if (any) {
         s = lh_alloc(ctx, &d_tot, 2 * LH_MAX_LEVELS);
         if (s == LH_OK) {
@@ -523,7 +557,8 @@ lh_status lh_trie_layout(lh_ctx *ctx, lh_trie *t) {
         if ((s = lh_alloc(ctx, &tmp_isbs[l], L.nsets)) != LH_OK) break;
         if ((s = lh_alloc(ctx, &tmp_words[l], L.nsets)) != LH_OK) break;
         LH_TRACED(ctx, "k_layout_decide", k_layout_decide<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
-            L.vals, poffs, L.nsets, (uint32_t)L.n, t->bs_ratio, t->bs_min_card, tmp_isbs[l], tmp_words[l], d_tot + 2 * l));
+            L.vals, poffs, L.nsets, (uint32_t)L.n, nullptr, nullptr, t->bs_ratio, t->bs_min_card, tmp_isbs[l],
+            tmp_words[l], d_tot + 2 * l));
     }
     if (s == LH_OK && any) s = lh_readback(ctx, d_tot, sizeof(h_tot), h_tot);
     lh_free(ctx, d_tot);
@@ -640,6 +675,8 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     const unsigned G = (unsigned)std::min<uint64_t>(lh_blocks(n, T), (uint64_t)ctx->num_sms * 16);
     const unsigned G4 = (unsigned)std::min<uint64_t>(lh_blocks((n + 3) / 4, T), (uint64_t)ctx->num_sms * 16);
 
+    LayoutPre pre;
+    memset(&pre, 0, sizeof(pre));
     uint32_t *d_max = nullptr, *ticket = nullptr;
     uint64_t *key = nullptr, *tkey = nullptr, *d_count = nullptr;
     uint32_t *rid = nullptr, *trid = nullptr, *runstart = nullptr;
@@ -653,6 +690,9 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         lh_free(ctx, lstate);
         for (uint32_t l = 0; l < L; ++l) { lh_free(ctx, tvals[l]); lh_free(ctx, toffs[l]); }
     };
+    auto free_pre = [&]() {
+        for (uint32_t l = 0; l < L; ++l) { lh_free(ctx, pre.isbs[l]); lh_free(ctx, pre.words[l]); }
+    };
 #define STEP(x) if (s == LH_OK) s = (x)
     // 1. key widths
     uint32_t bits[LH_MAX_LEVELS] = {0};
@@ -661,20 +701,31 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     memset(&pa, 0, sizeof(pa));
     pa.nlev = L;
     for (uint32_t l = 0; l < L; ++l) pa.col[l] = rel->keys[key_order[l]];
-    STEP(lh_alloc(ctx, &d_max, L));
-    if (s == LH_OK) {
-        cudaMemsetAsync(d_max, 0, L * sizeof(uint32_t), ctx->stream);
-        if (n) LH_TRACED(ctx, "k_col_max", k_col_max<<<G4, T, 0, ctx->stream>>>(pa, n, d_max));
-        uint32_t hmax[LH_MAX_LEVELS] = {0};
-        STEP(lh_readback(ctx, d_max, L * sizeof(uint32_t), hmax));
+    bool bounded = true;
+    for (uint32_t l = 0; l < L; ++l) bounded = bounded && rel->key_bound[key_order[l]] != 0;
+    if (bounded) {
+        // declared domains: widths without reading the columns (k_pack checks them)
         for (uint32_t l = 0; l < L; ++l) {
-            bits[l] = hmax[l] ? 32 - __builtin_clz(hmax[l]) : 1;
-            t->key_bits[l] = bits[l];
-            total_bits += bits[l];
+            const uint32_t b = rel->key_bound[key_order[l]];
+            pa.bound[l] = b;
+            bits[l] = b > 1 ? 32 - __builtin_clz(b - 1) : 1;
         }
-        if (s == LH_OK && total_bits > 64)
-            s = lh_fail(ctx, LH_EUNSUPPORTED, "packed key needs %u > 64 bits", total_bits);
+    } else {
+        STEP(lh_alloc(ctx, &d_max, L));
+        if (s == LH_OK) {
+            cudaMemsetAsync(d_max, 0, L * sizeof(uint32_t), ctx->stream);
+            if (n) LH_TRACED(ctx, "k_col_max", k_col_max<<<G4, T, 0, ctx->stream>>>(pa, n, d_max));
+            uint32_t hmax[LH_MAX_LEVELS] = {0};
+            STEP(lh_readback(ctx, d_max, L * sizeof(uint32_t), hmax));
+            for (uint32_t l = 0; l < L; ++l) bits[l] = hmax[l] ? 32 - __builtin_clz(hmax[l]) : 1;
+        }
     }
+    for (uint32_t l = 0; l < L; ++l) {
+        t->key_bits[l] = bits[l];
+        total_bits += bits[l];
+    }
+    if (s == LH_OK && total_bits > 64)
+        s = lh_fail(ctx, LH_EUNSUPPORTED, "packed key needs %u > 64 bits", total_bits);
     // 2. pack + sort
     uint32_t shift[LH_MAX_LEVELS];
     {
@@ -694,12 +745,15 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     STEP(lh_alloc(ctx, &tkey, n));
     STEP(lh_alloc(ctx, &rid, n));
     STEP(lh_alloc(ctx, &trid, n));
-    // level counts, then one status word (sort and level waits) read back together
-    STEP(lh_alloc(ctx, &d_count, L + 1));
+    // one readback block: level counts, the status word (key bounds, sort and
+    // level waits), then the layout totals (bitset sets, words) per level
+    const size_t n_rb = L + 1 + 2 * LH_MAX_LEVELS;
+    STEP(lh_alloc(ctx, &d_count, n_rb));
     if (s == LH_OK) {
-        cudaError_t e = cudaMemsetAsync(d_count, 0, (L + 1) * sizeof(uint64_t), ctx->stream);
+        cudaError_t e = cudaMemsetAsync(d_count, 0, n_rb * sizeof(uint64_t), ctx->stream);
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie: %s", cudaGetErrorString(e));
     }
+    pa.status = d_count ? (uint32_t *)(d_count + L) : nullptr;
     if (s == LH_OK && n) {
         LH_TRACED(ctx, "k_pack", k_pack<<<G4, T, 0, ctx->stream>>>(pa, n, key, rid));
         STEP(lh_radix_sort_u64(ctx, &key, &rid, &tkey, &trid, n, (int)total_bits, (uint32_t *)(d_count + L)));
@@ -715,7 +769,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         STEP(lh_alloc(ctx, &tvals[l], n));
         STEP(lh_alloc(ctx, &toffs[l], n + 1));
     }
-    uint64_t cnt[LH_MAX_LEVELS + 1] = {0};
+    uint64_t cnt[3 * LH_MAX_LEVELS + 1] = {0};
     if (s == LH_OK && n) {
         if (ntiles >= (1ull << 32)) s = lh_fail(ctx, LH_EOVERFLOW, "too many level tiles");
         LevelArgs la;
@@ -745,9 +799,28 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
                 default: LH_TRACED(ctx, "k_levels", k_levels<6><<<nt, kLvThreads, 0, ctx->stream>>>(key, n, la)); break;
             }
         }
-        STEP(lh_readback(ctx, d_count, (L + 1) * sizeof(uint64_t), cnt));
+        // layout decisions on the level arrays as written (upper levels still
+        // in their temporaries), set counts read on the device
+        if (s == LH_OK && pol.bs_ratio != 0) {
+            unsigned long long *d_tot = (unsigned long long *)(d_count + L + 1);
+            for (uint32_t l = 0; l < L && s == LH_OK; ++l) {
+                const uint64_t cap_sets = l ? n : 1;
+                STEP(lh_alloc(ctx, &pre.isbs[l], cap_sets));
+                STEP(lh_alloc(ctx, &pre.words[l], cap_sets));
+                if (s != LH_OK) break;
+                const uint32_t *lv_vals = l + 1 < L ? tvals[l] : t->lv[l].vals;
+                const uint32_t *poffs = l ? toffs[l - 1] : nullptr;
+                LH_TRACED(ctx, "k_layout_decide", k_layout_decide<<<lh_blocks(cap_sets, T, (uint32_t)ctx->num_sms * 16), T, 0, ctx->stream>>>(
+                    lv_vals, poffs, 1, 0, l ? d_count + (l - 1) : nullptr, d_count + l, pol.bs_ratio,
+                    pol.bs_min_card, pre.isbs[l], pre.words[l], d_tot + 2 * l));
+            }
+        }
+        STEP(lh_readback(ctx, d_count, n_rb * sizeof(uint64_t), cnt));
+        if (s == LH_OK) memcpy(pre.tot, cnt + L + 1, sizeof(pre.tot));
         if (s == LH_OK && (uint32_t)cnt[L])
-            s = lh_fail(ctx, (lh_status)(uint32_t)cnt[L], "build_trie: a bounded wait (sort or level offsets) gave up");
+            s = lh_fail(ctx, (lh_status)(uint32_t)cnt[L], (uint32_t)cnt[L] == LH_EINVAL
+                                                              ? "build_trie: a key value is at or above its key_bound"
+                                                              : "build_trie: a bounded wait (sort or level offsets) gave up");
     }
     for (uint32_t l = 0; l < L; ++l) t->lv[l].n = cnt[l];
     nu = cnt[L - 1];
@@ -818,7 +891,9 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie: %s", cudaGetErrorString(e));
     }
     cleanup_tmp();
-    STEP(lh_trie_layout(ctx, t));
+    if (s == LH_OK && n && pol.bs_ratio != 0) s = trie_layout(ctx, t, &pre);
+    else STEP(lh_trie_layout(ctx, t));
+    free_pre();
 #undef STEP
     if (s != LH_OK) {
         lh_trie_release(ctx, t);

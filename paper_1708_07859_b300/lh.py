@@ -46,7 +46,8 @@ class LHError(RuntimeError):
 class RelationDesc(C.Structure):
     _fields_ = [("nrows", C.c_uint64), ("nkeys", C.c_uint32),
                 ("keys", C.c_void_p * MAX_LEVELS), ("nannos", C.c_uint32),
-                ("annos", C.c_void_p * MAX_ANNOS), ("anno_types", C.c_uint32 * MAX_ANNOS)]
+                ("annos", C.c_void_p * MAX_ANNOS), ("anno_types", C.c_uint32 * MAX_ANNOS),
+                ("key_bound", C.c_uint32 * MAX_LEVELS)]
 
 
 class LayoutPolicy(C.Structure):
@@ -262,10 +263,13 @@ class Context:
         self._check(lib().lh_set_stream(self.h, C.c_void_p(s.cuda_stream)))
 
     # --- tries -----------------------------------------------------------
-    def build_trie(self, keys, key_order=None, annos=(), merge=MERGE_SUM, layout=None):
+    def build_trie(self, keys, key_order=None, annos=(), merge=MERGE_SUM, layout=None, key_bounds=None):
         """keys: list of CUDA int32/uint32 tensors (same length); annos: list
-        of (tensor, lh_dtype).  Returns a Trie."""
+        of (tensor, lh_dtype); key_bounds: optional domain size per key
+        column (every value below it).  Returns a Trie."""
         desc = RelationDesc()
+        for i, b in enumerate(key_bounds or ()):
+            desc.key_bound[i] = int(b)
         desc.nrows = int(keys[0].numel()) if keys else 0
         desc.nkeys = len(keys)
         for i, k in enumerate(keys):
@@ -636,9 +640,11 @@ def spgemm_query(card_a, card_b):
                       materialized=(0, 2))
 
 
-def matrix_trie(ctx, rows, cols, vals, layout=None):
+def matrix_trie(ctx, rows, cols, vals, layout=None, dims=None):
+    """Trie of a COO matrix (levels row, column; f32 values summed over
+    duplicates).  dims = (rows, cols) declares the key domains."""
     return ctx.build_trie([rows, cols], key_order=[0, 1], annos=[(vals, T_F32)], merge=MERGE_SUM,
-                          layout=layout)
+                          layout=layout, key_bounds=dims)
 
 
 # ---------------------------------------------------------- batched joins

@@ -175,3 +175,24 @@ def test_empty_relation(ctx):
     st = tr.stats()
     assert st.level_n[0] == 0 and st.level_n[1] == 0
     tr.free()
+
+
+def test_declared_key_bounds(ctx, orc):
+    """Key domains declared by the caller give the same trie as the maxima
+    read from the columns; a value at or above its bound is refused."""
+    from paper_1708_07859_b300 import lh
+    rng = np.random.default_rng(12)
+    n = 7000
+    cols = [rng.integers(0, 300, n), rng.integers(0, 5000, n)]
+    dcols = [dev_u32(c) for c in cols]
+    want = orc.trie_levels(cols, (0, 1))
+    for bounds in ((300, 5000), (1 << 12, 1 << 20)):
+        tr = ctx.build_trie(dcols, key_bounds=bounds)
+        arrays = [tr.level_arrays(l) for l in range(2)]
+        assert np.array_equal(arrays[0]["vals"], want[0][0])
+        assert np.array_equal(arrays[1]["vals"], want[1][0])
+        assert np.array_equal(arrays[0]["offs"].astype(np.uint64), want[1][1])
+        tr.free()
+    with pytest.raises(lh.LHError) as e:
+        ctx.build_trie(dcols, key_bounds=(300, 4000))
+    assert e.value.status == lh.EINVAL
