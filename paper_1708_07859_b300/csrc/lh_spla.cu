@@ -20,6 +20,11 @@ namespace {
 constexpr int kSpmvThreads = 256;
 constexpr int kSpmvGroup = 16;
 
+// Each 16-lane group handles kSpmvRows rows per iteration (rows g, g + G,
+// ...), so their offset loads, first element loads and x gathers are all in
+// flight together; rows longer than 16 entries finish in a loop.
+constexpr int kSpmvRows = 4;
+
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv(DTrie A, const float *av, const float *x,
                                                        uint32_t x_n, uint32_t nrow_entries, float *y) {
     const int lane = threadIdx.x & 31;
@@ -27,27 +32,56 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(DTrie A, const float *av,
     const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / kSpmvGroup;
     const uint32_t ngroups = (gridDim.x * blockDim.x) / kSpmvGroup;
     const uint32_t *rows = A.lv[0].vals, *offs = A.lv[0].offs, *cols = A.lv[1].vals;
-    for (uint32_t p0 = group - (group % 2); p0 < nrow_entries; p0 += ngroups) {
+    const uint64_t stride = (uint64_t)ngroups * kSpmvRows;
+    for (uint64_t p0 = group - (group % 2); p0 < nrow_entries; p0 += stride) {
         // both half-warps iterate together so the shuffles stay converged
-        const uint32_t p = p0 + (group % 2);
-        const bool valid = p < nrow_entries;
-        float sh = 0.f, sl = 0.f;
-        if (valid) {
-            const uint32_t lo = __ldg(offs + p), hi = __ldg(offs + p + 1);
-            for (uint32_t q = lo + sub; q < hi; q += kSpmvGroup) {
-                const uint32_t j = __ldg(cols + q);
-                if (j >= x_n) continue;  // x holds keys [0, x_n) only
+        uint32_t lo[kSpmvRows], hi[kSpmvRows];
+        bool valid[kSpmvRows];
+#pragma unroll
+        for (int u = 0; u < kSpmvRows; ++u) {
+            const uint64_t p = p0 + (group % 2) + (uint64_t)u * ngroups;
+            valid[u] = p < nrow_entries;
+            lo[u] = valid[u] ? __ldg(offs + p) : 0u;
+            hi[u] = valid[u] ? __ldg(offs + p + 1) : 0u;
+        }
+        uint32_t j[kSpmvRows];
+        float a[kSpmvRows], xv[kSpmvRows];
+#pragma unroll
+        for (int u = 0; u < kSpmvRows; ++u) {
+            const uint32_t q = lo[u] + sub;
+            const bool in = q < hi[u];
+            j[u] = in ? __ldg(cols + q) : 0xFFFFFFFFu;
+            a[u] = in ? __ldg(av + q) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kSpmvRows; ++u) xv[u] = j[u] < x_n ? __ldg(x + j[u]) : 0.f;  // x holds keys [0, x_n)
+        float sh[kSpmvRows], sl[kSpmvRows];
+#pragma unroll
+        for (int u = 0; u < kSpmvRows; ++u) {
+            sh[u] = 0.f;
+            sl[u] = 0.f;
+            if (j[u] < x_n) {
                 float ph, pl;
-                lh_two_prod(__ldg(av + q), __ldg(x + j), ph, pl);
-                lh_pair_add(sh, sl, ph, pl);
+                lh_two_prod(a[u], xv[u], ph, pl);
+                lh_pair_add(sh[u], sl[u], ph, pl);
+            }
+            for (uint32_t q = lo[u] + sub + kSpmvGroup; q < hi[u]; q += kSpmvGroup) {
+                const uint32_t jj = __ldg(cols + q);
+                if (jj >= x_n) continue;
+                float ph, pl;
+                lh_two_prod(__ldg(av + q), __ldg(x + jj), ph, pl);
+                lh_pair_add(sh[u], sl[u], ph, pl);
             }
         }
 #pragma unroll
-        for (int o = kSpmvGroup / 2; o > 0; o >>= 1) {
-            float oh = __shfl_xor_sync(LH_FULL, sh, o), ol = __shfl_xor_sync(LH_FULL, sl, o);
-            lh_pair_add(sh, sl, oh, ol);
+        for (int u = 0; u < kSpmvRows; ++u) {
+#pragma unroll
+            for (int o = kSpmvGroup / 2; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(LH_FULL, sh[u], o), ol = __shfl_xor_sync(LH_FULL, sl[u], o);
+                lh_pair_add(sh[u], sl[u], oh, ol);
+            }
+            if (valid[u] && sub == 0) y[__ldg(rows + p0 + (group % 2) + (uint64_t)u * ngroups)] = sh[u] + sl[u];
         }
-        if (valid && sub == 0) y[__ldg(rows + p)] = sh + sl;
     }
 }
 
