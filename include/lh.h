@@ -10,11 +10,14 @@
  *     copied during the call.  Device inputs are caller-owned and must stay
  *     valid until the work that reads them is complete (lh_sync /
  *     lh_result_wait).
- *   - All work is issued asynchronously on the context's CUDA stream.  The
- *     generic join driver reads frontier sizes back to the host between
- *     chunks (it synchronises the stream there); every other call only
- *     enqueues work.  Device-side error words (overflow, bounded-wait
- *     timeouts) surface at lh_sync / lh_result_wait.
+ *   - All work is issued asynchronously on the context's CUDA stream.  Calls
+ *     that size an allocation from device data read a few words back and so
+ *     synchronise the stream there: lh_build_trie (level sizes and bitset
+ *     totals, plus the key maxima when no key_bound is given), the SpGEMM
+ *     path of lh_join_aggregate (the product bound), and the generic join
+ *     driver (frontier sizes between chunks).  Device-side error words
+ *     (overflow, bounded-wait timeouts) surface at the call's own readback,
+ *     at lh_sync or at lh_result_wait.
  *   - Objects returned through out-pointers (tries, results, models,
  *     batches) own device memory until their *_free call.
  */
@@ -378,7 +381,8 @@ typedef struct {
  * columns are supported by the generic driver. */
 lh_status lh_join_aggregate(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
                             lh_trie *const *tries, lh_result **out);
-/* Wait for the result and fill `view` (host struct; device pointers inside). */
+/* Wait for the result and fill `view` (host struct; device pointers inside;
+ * for SPGEMM this is where nnz is read back). */
 lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *view);
 lh_status lh_result_free(lh_ctx *ctx, lh_result *r);
 

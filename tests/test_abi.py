@@ -41,3 +41,12 @@ def test_struct_sizes_match_header_layout(lhlib):
     assert ctypes.sizeof(lhlib.Set) == 24
     assert ctypes.sizeof(lhlib.Edge) == 4 + 4 + 24 + 4 + 4 + 8 + 8 + 8
     assert ctypes.sizeof(lhlib.Group) == 16
+
+
+def test_committed_dram_traffic_matches_the_kernel_source():
+    """The DRAM traffic the bench reports for its dominant kernel comes from a
+    committed ncu capture keyed by a hash of the kernel's source; the capture
+    is current for the source as committed (the bench reports null otherwise)."""
+    import bench
+    assert bench.dram_traffic("k_spgemm_esc", 1 << 19) == 1096105472
+    assert bench.dram_traffic("k_spgemm_esc", 1 << 20) == 2 * 1096105472
