@@ -77,9 +77,9 @@ __global__ void k_pack(PackArgs a, uint64_t n, uint64_t *key, uint32_t *rid) {
 // ---- CSR levels from the sorted packed keys, in one pass ------------------
 // Level l's prefix of key k is k >> shift[l] (levels 0..l); a sorted row i
 // opens a level-l entry when that prefix differs from row i-1's.  A tile of
-// 2048 rows is staged in shared memory; thread t takes rows j * 256 + t, so
-// the entries a warp opens for one j land at consecutive indices (ballot +
-// popc) and its stores coalesce.  Warp l scans the tile's per-(j, warp)
+// 4096 rows (2048 beyond three levels) is staged in shared memory; thread t
+// takes rows j * 256 + t, so the entries a warp opens for one j land at
+// consecutive indices (ballot + popc) and its stores coalesce.  Warp l scans the tile's per-(j, warp)
 // counts of level l, finds the tile's offset in level l by decoupled
 // look-back over tile tickets, and then every opened entry writes its value,
 // its first child's index in the level below and (leaf level) the first
@@ -88,8 +88,10 @@ __global__ void k_pack(PackArgs a, uint64_t n, uint64_t *key, uint32_t *rid) {
 // waiting.
 constexpr int kLvThreads = 256;
 constexpr int kLvWarps = kLvThreads / 32;
-constexpr int kLvItems = 8;
-constexpr uint64_t kLvTile = (uint64_t)kLvThreads * kLvItems;
+// rows per thread: 16 (4096-row tiles) for up to three levels, 8 beyond,
+// where the per-level ballot words would spill
+__host__ __device__ constexpr int lv_items(int nl) { return nl <= 3 ? 16 : 8; }
+__host__ __device__ constexpr uint64_t lv_tile(int nl) { return (uint64_t)kLvThreads * lv_items(nl); }
 constexpr unsigned long long kLvAgg = 1ull << 62, kLvInc = 1ull << 63, kLvVal = (1ull << 62) - 1;
 constexpr uint32_t kLvSpins = 1u << 20;
 
@@ -117,6 +119,9 @@ __device__ __forceinline__ unsigned long long lv_load(const unsigned long long *
 
 template <int NL>
 __global__ void __launch_bounds__(kLvThreads) k_levels(const uint64_t *key, uint64_t n, LevelArgs a) {
+    constexpr int kLvItems = lv_items(NL);
+    constexpr uint64_t kLvTile = lv_tile(NL);
+    constexpr int kPer = kLvItems * kLvWarps / 32;  // (j, warp) counts per lane in the scan
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_ok;
     __shared__ uint64_t s_k[kLvTile];
@@ -156,17 +161,26 @@ __global__ void __launch_bounds__(kLvThreads) k_levels(const uint64_t *key, uint
     __syncthreads();
     if (warp < NL) {
         const uint32_t l = warp;
-        // exclusive scan of the 64 (j, warp) counts in row order; lane holds two
-        const uint32_t c0 = s_base[l][2 * lane], c1 = s_base[l][2 * lane + 1];
-        uint32_t incl = c0 + c1;
+        // exclusive scan of the (j, warp) counts in row order; lane holds kPer
+        uint32_t cc[kPer];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            cc[i] = s_base[l][kPer * lane + i];
+            mine += cc[i];
+        }
+        uint32_t incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x = __shfl_up_sync(LH_FULL, incl, o);
             if (lane >= o) incl += x;
         }
-        const uint32_t ex = incl - c0 - c1;
-        s_base[l][2 * lane] = ex;
-        s_base[l][2 * lane + 1] = ex + c0;
+        uint32_t run = incl - mine;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            s_base[l][kPer * lane + i] = run;
+            run += cc[i];
+        }
         const uint64_t agg = __shfl_sync(LH_FULL, incl, 31);
         // publish the tile's count, then look back for its offset
         if (lane == 0) lv_store(a.state + (uint64_t)tile * NL + l, (tile == 0 ? kLvInc : kLvAgg) | agg);
@@ -760,7 +774,8 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     }
     // 3. levels: the leaf level is written in place (capacity n), the levels
     //    above into temporaries, copied out once their sizes are known
-    const uint64_t ntiles = (n + kLvTile - 1) / kLvTile;
+    const uint64_t lvt = lv_tile((int)L);
+    const uint64_t ntiles = (n + lvt - 1) / lvt;
     STEP(trie_alloc(ctx, t, &t->lv[L - 1].vals, n));
     STEP(lh_alloc(ctx, &runstart, n));
     STEP(lh_alloc(ctx, &ticket, 1));
