@@ -497,10 +497,14 @@ def run_reference(args):
             vals.append(cb["value"])
         base = cb
     v = statistics.mean(vals) if vals else base["value"]
+    elems, _ = step_elements(A, B)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gelem/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup,
+            # the oracle's time for one whole step's elements at its measured rate
+            "ms_per_step": elems / (v * 1e9) * 1e3 if v else None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": CONFIG_NAME, "rows": args.rows},
+            "config": {"workload": CONFIG_NAME, "rows": args.rows, "nnz_per_row": PER_ROW, "zipf_s": 1.1,
+                       "elements_per_step": elems, "parallelism": "host cores"},
             "cpu_baseline": dict(base, value=v),
             "e2e": {"value": v, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
