@@ -583,7 +583,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_onesweep(
 }  // namespace
 
 lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint64_t **tmp_k,
-                            uint32_t **tmp_v, uint64_t n, int bits, uint32_t *status_out) {
+                            uint32_t **tmp_v, uint64_t n, int bits, uint32_t *status_out,
+                            const unsigned long long *hist_in) {
     if (n <= 1 || bits <= 0) return LH_OK;
     const uint64_t ntiles64 = (n + kSortTile - 1) / kSortTile;
     if (ntiles64 > (1u << 24)) return lh_fail(ctx, LH_EUNSUPPORTED, "sort: too many keys");
@@ -605,15 +606,16 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint6
             e = cudaFuncSetAttribute(k_sort_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort setup: %s", cudaGetErrorString(e));
     }
-    if (s == LH_OK) {
+    if (s == LH_OK && !hist_in) {
         const unsigned g = (unsigned)std::min<uint64_t>(lh_blocks((n + 3) / 4, 256), (uint64_t)ctx->num_sms * 8);
         LH_TRACED(ctx, "k_sort_upsweep", k_sort_upsweep<<<g, 256, 0, ctx->stream>>>(*keys, n, passes, ghist));
     }
+    const unsigned long long *hist = hist_in ? hist_in : ghist;
     uint64_t *ka = *keys, *kb = *tmp_k;
     uint32_t *va = *vals, *vb = *tmp_v;
     for (int p = 0; p < passes && s == LH_OK; ++p) {
         LH_TRACED(ctx, "k_sort_onesweep", k_sort_onesweep<<<ntiles, kSortThreads, kScatterSmem, ctx->stream>>>(
-                                              ka, va, n, 8 * p, ghist + (size_t)p * 256,
+                                              ka, va, n, 8 * p, hist + (size_t)p * 256,
                                               state + (size_t)p * ntiles * 256, tickets + p, status, kb, vb));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "sort: %s", cudaGetErrorString(e));

@@ -116,9 +116,12 @@ lh_status lh_scan_u64_to_u64(lh_ctx *ctx, const uint64_t *in, uint64_t *out, uin
 // return the pointers are swapped as needed so that (*keys, *vals) hold the
 // sorted pairs and (*tmp_k, *tmp_v) the scratch.  status: a zeroed device
 // word that receives LH_ETIMEOUT if a bounded wait gives up (the caller
-// reads it back), or null for the sort to read its own back.
+// reads it back), or null for the sort to read its own back.  hist: the
+// 256-bin digit counts of every pass (pass p at hist[256 p]) when the caller
+// has counted them already, or null for the sort to count them.
 lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint64_t **tmp_k,
-                            uint32_t **tmp_v, uint64_t n, int bits, uint32_t *status);
+                            uint32_t **tmp_v, uint64_t n, int bits, uint32_t *status,
+                            const unsigned long long *hist = nullptr);
 
 // ----------------------------------------------------------------------- tries
 

@@ -14,6 +14,8 @@ struct PackArgs {
     uint32_t nlev;
     const uint32_t *payload;  // 4-byte annotation carried through the sort, or null: row ids
     uint32_t *status;         // LH_EINVAL when a value breaks its bound
+    unsigned long long *hist; // digit counts of every sort pass (pass p at hist[256 p]), zeroed
+    int passes;
 };
 
 // Largest value of every key column, one launch: each thread takes four
@@ -45,6 +47,11 @@ __global__ void k_col_max(PackArgs a, uint64_t n, uint32_t *out) {
 // Packed key (level 0 in the high bits) and sort payload of every row; four
 // rows per thread and grid stride, loaded before they are stored.
 __global__ void k_pack(PackArgs a, uint64_t n, uint64_t *key, uint32_t *rid) {
+    // the radix sort's digit counts of every pass, counted while the keys are
+    // in registers (per-block shared histograms, folded into a.hist at the end)
+    __shared__ uint32_t h[8][256];
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
         uint64_t k[4] = {0, 0, 0, 0};
@@ -70,7 +77,13 @@ __global__ void k_pack(PackArgs a, uint64_t n, uint64_t *key, uint32_t *rid) {
             if (i + u * stride < n) {
                 key[i + u * stride] = k[u];
                 rid[i + u * stride] = r[u];
+                for (int p = 0; p < a.passes; ++p) atomicAdd(&h[p][(k[u] >> (8 * p)) & 255u], 1u);
             }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(a.hist + i, (unsigned long long)c);
     }
 }
 
@@ -693,6 +706,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     memset(&pre, 0, sizeof(pre));
     uint32_t *d_max = nullptr, *ticket = nullptr;
     uint64_t *key = nullptr, *tkey = nullptr, *d_count = nullptr;
+    unsigned long long *d_hist = nullptr;
     uint32_t *rid = nullptr, *trid = nullptr, *runstart = nullptr;
     unsigned long long *lstate = nullptr;
     std::vector<uint32_t *> tvals(L, nullptr), toffs(L, nullptr);
@@ -700,7 +714,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     lh_status s = LH_OK;
     auto cleanup_tmp = [&]() {
         lh_free(ctx, d_max); lh_free(ctx, ticket); lh_free(ctx, key); lh_free(ctx, tkey);
-        lh_free(ctx, d_count); lh_free(ctx, rid); lh_free(ctx, trid); lh_free(ctx, runstart);
+        lh_free(ctx, d_count); lh_free(ctx, d_hist); lh_free(ctx, rid); lh_free(ctx, trid); lh_free(ctx, runstart);
         lh_free(ctx, lstate);
         for (uint32_t l = 0; l < L; ++l) { lh_free(ctx, tvals[l]); lh_free(ctx, toffs[l]); }
     };
@@ -768,9 +782,16 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie: %s", cudaGetErrorString(e));
     }
     pa.status = d_count ? (uint32_t *)(d_count + L) : nullptr;
+    pa.passes = (int)((total_bits + 7) / 8);
+    STEP(lh_alloc(ctx, &d_hist, (size_t)8 * 256));
+    if (s == LH_OK) {
+        cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)8 * 256 * sizeof(unsigned long long), ctx->stream);
+        if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie: %s", cudaGetErrorString(e));
+    }
+    pa.hist = d_hist;
     if (s == LH_OK && n) {
         LH_TRACED(ctx, "k_pack", k_pack<<<G4, T, 0, ctx->stream>>>(pa, n, key, rid));
-        STEP(lh_radix_sort_u64(ctx, &key, &rid, &tkey, &trid, n, (int)total_bits, (uint32_t *)(d_count + L)));
+        STEP(lh_radix_sort_u64(ctx, &key, &rid, &tkey, &trid, n, (int)total_bits, (uint32_t *)(d_count + L), d_hist));
     }
     // 3. levels: the leaf level is written in place (capacity n), the levels
     //    above into temporaries, copied out once their sizes are known
