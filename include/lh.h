@@ -79,6 +79,13 @@ lh_status lh_set_stream(lh_ctx *ctx, void *cuda_stream);
  * sizes are carved from one mapping instead of growing the pool call by
  * call.  Blocks until done; LH_ENOMEM if the device cannot provide it. */
 lh_status lh_pool_reserve(lh_ctx *ctx, uint64_t bytes);
+/* Bytes of the context's pool handed out right now (used_now) and the most
+ * ever handed out at once since the last reset (used_high); either pointer
+ * may be NULL.  reset_high != 0 then restarts the high-water mark at the
+ * current use.  Read on the host without waiting for the stream: call
+ * lh_sync first to see the work issued so far.  No paper counterpart; a
+ * diagnostic of this library's memory management. */
+lh_status lh_pool_usage(lh_ctx *ctx, uint64_t *used_now, uint64_t *used_high, int reset_high);
 /* Last error message of this context (never NULL). */
 const char *lh_last_error(const lh_ctx *ctx);
 /* Wait for the stream; return the first device-side error word, if any. */
@@ -343,6 +350,17 @@ typedef struct {
 lh_status lh_plan(lh_ctx *ctx, const lh_query *q, lh_planner_kind kind, const lh_model *model,
                   const lh_relation_desc *const *rels, const lh_plan_opts *opts, lh_plan_t *out);
 
+/* The Section 4 cost terms of running q in `order` (host array of
+ * q->n_attrs attribute ids, a permutation): icost[i] (host, n_attrs
+ * entries) of order position i under the layout guesses of Section 4.1.1,
+ * weight[a] (host, n_attrs entries) of attribute a per Section 4.2 from the
+ * edges' cardinalities, and *cost = sum_i icost[i] * weight[order[i]].  Any
+ * output pointer may be NULL.  The same arithmetic LH_PLANNER_COST
+ * minimises; no device work.  LH_EINVAL for a bad order or an edge whose
+ * cardinality is unknown. */
+lh_status lh_plan_explain(lh_ctx *ctx, const lh_query *q, const uint32_t *order, int32_t *icost,
+                          int64_t *weight, int64_t *cost);
+
 /* Key order (host array, edge's nattrs entries) of the trie edge `e` must be
  * built with under `plan`: its key columns sorted by position in plan->order. */
 lh_status lh_edge_key_order(const lh_query *q, const lh_plan_t *plan, uint32_t e,
@@ -431,8 +449,11 @@ lh_status lh_batch_create(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs,
 /* Replay the captured graph on the context stream. */
 lh_status lh_batch_run(lh_ctx *ctx, lh_batch *b);
 lh_status lh_batch_free(lh_ctx *ctx, lh_batch *b);
-/* Sweep tunings on the batch (successive halving over a grid) and return the
- * fastest; best_ms: its replay time. */
+/* Sweep tunings (successive halving over a grid of t_warp, chunk and
+ * ctas_per_sm) and return the fastest.  The candidates are timed on a fixed
+ * sample of the batch -- every 4th query, or all of them when n < 8 -- so the
+ * other queries stay out of the tuning.  best_ms: the winner's replay time on
+ * that sample.  counts (device uint64[n]) is scratch while tuning. */
 lh_status lh_batch_autotune(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs, uint64_t *counts,
                             lh_batch_tuning *best, float *best_ms);
 

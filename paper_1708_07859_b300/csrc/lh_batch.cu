@@ -253,10 +253,22 @@ extern "C" lh_status lh_batch_free(lh_ctx *ctx, lh_batch *b) {
 }
 
 // Grid of tunings, successive halving: every candidate is timed once, the
-// faster third is timed three more times, the best mean wins.
-extern "C" lh_status lh_batch_autotune(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs, uint64_t *counts,
+// faster third is timed three more times, the best mean wins.  The timings
+// run on a fixed sample of the batch -- every kTuneStride-th query (all of
+// them for batches below 2 * kTuneStride) -- so the remaining queries are
+// held out of the tuning and the full batch measures the chosen thresholds
+// on mostly unseen work.
+constexpr uint32_t kTuneStride = 4;
+
+extern "C" lh_status lh_batch_autotune(lh_ctx *ctx, uint32_t n_all, const lh_batch_query *qs_all, uint64_t *counts,
                                        lh_batch_tuning *best, float *best_ms) {
     if (!ctx || !best) return lh_fail(ctx, LH_EINVAL, "null argument");
+    if (n_all == 0 || !qs_all || !counts) return lh_fail(ctx, LH_EINVAL, "empty batch");
+    std::vector<lh_batch_query> sample;
+    const uint32_t stride = n_all >= 2 * kTuneStride ? kTuneStride : 1u;
+    for (uint32_t i = 0; i < n_all; i += stride) sample.push_back(qs_all[i]);
+    const uint32_t n = (uint32_t)sample.size();
+    const lh_batch_query *qs = sample.data();
     struct Cand { lh_batch_tuning t; double ms; int runs; };
     std::vector<Cand> cands;
     const uint32_t tw[] = {64, 256, 2048};

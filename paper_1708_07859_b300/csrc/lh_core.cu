@@ -87,6 +87,20 @@ extern "C" lh_status lh_pool_reserve(lh_ctx *ctx, uint64_t bytes) {
     return LH_OK;
 }
 
+extern "C" lh_status lh_pool_usage(lh_ctx *ctx, uint64_t *used_now, uint64_t *used_high, int reset_high) {
+    if (!ctx || !ctx->pool) return LH_EINVAL;
+    unsigned long long now = 0, high = 0;  // the pool attributes are 64-bit
+    LH_CU(cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &now));
+    LH_CU(cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &high));
+    if (used_now) *used_now = now;
+    if (used_high) *used_high = high;
+    if (reset_high) {
+        unsigned long long zero = 0;  // resets the high-water mark to the current use
+        LH_CU(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    return LH_OK;
+}
+
 extern "C" lh_status lh_set_stream(lh_ctx *ctx, void *stream) {
     if (!ctx) return LH_EINVAL;
     ctx->stream = (cudaStream_t)stream;
@@ -104,7 +118,11 @@ extern "C" lh_status lh_sync(lh_ctx *ctx) {
     LH_CU(cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost));
     if (st != 0) {
         LH_CU(cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
-        return lh_fail(ctx, (lh_status)st, "device-side error %u", st);
+        const char *what = st == LH_EINVAL      ? "a value outside its declared domain (key bound or GROUP BY card)"
+                           : st == LH_ETIMEOUT   ? "a bounded wait gave up"
+                           : st == LH_EOVERFLOW  ? "a 32-bit offset or capacity overflowed"
+                                                 : "error";
+        return lh_fail(ctx, (lh_status)st, "device-side error %u: %s", st, what);
     }
     return LH_OK;
 }
@@ -591,8 +609,9 @@ lh_status lh_radix_sort_u64(lh_ctx *ctx, uint64_t **keys, uint32_t **vals, uint6
     const uint32_t ntiles = (uint32_t)ntiles64;
     const int passes = (bits + 7) / 8;
     if (passes > kSortMaxPasses) return lh_fail(ctx, LH_EINVAL, "sort: more than 64 key bits");
-    // one zeroed block: histograms, look-back states, tickets, status
-    const size_t n_hist = (size_t)passes * 256, n_state = (size_t)passes * ntiles * 256;
+    // one zeroed block: histograms (unless the caller counted them), look-back
+    // states, tickets, status
+    const size_t n_hist = hist_in ? 0 : (size_t)passes * 256, n_state = (size_t)passes * ntiles * 256;
     const size_t words = n_hist + n_state + (size_t)(passes + 2) / 2 + 1;
     unsigned long long *scratch = nullptr;
     LH_TRY(lh_alloc(ctx, &scratch, words));

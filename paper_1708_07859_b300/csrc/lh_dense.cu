@@ -30,6 +30,10 @@ constexpr uint32_t kStageBytes = 2 * kATile + 2 * kBTile;  // A_hi, A_lo, B_hi, 
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr uint32_t kSpinLimit = 1u << 22;
+// After a wait gave up, copies or MMAs already issued may still complete into
+// shared or tensor memory; before the CTA releases either, the same phase is
+// polled again with this much longer bound (no new work is issued meanwhile).
+constexpr uint32_t kDrainLimit = 1u << 26;
 
 // kind::f16 instruction descriptor: fp32 D, bf16 A and B, both K-major,
 // N = 256 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
@@ -91,8 +95,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
 }
 
 // bounded wait on a phase; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
@@ -196,9 +200,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_2d(st + 2 * kATile + kBTile, &tBl, &full[s], kb * BK, n0);
             issued = kb + 1;
         }
-        // let the last loads land before the CTA can leave (bounded)
+        // let the last loads land before the CTA can leave: after a timeout
+        // these may be the copies that were late, hence the drain bound
         for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-            mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+            if (!mbar_wait(&full[kb % kStages], (kb / kStages) & 1, kDrainLimit)) lh_set_status(status, LH_ETIMEOUT);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         for (int kb = 0; kb < nk; ++kb) {
@@ -226,7 +231,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma_commit(done);
     }
     __syncwarp();
-    if (!mbar_wait(done, 0)) lh_set_status(status, LH_ETIMEOUT);
+    if (!mbar_wait(done, 0)) {
+        // the MMAs issued so far may still be writing tensor memory: drain
+        // them (the commit on `done` follows the last issued MMA) before the
+        // epilogue reads and the CTA frees that memory
+        lh_set_status(status, LH_ETIMEOUT);
+        mbar_wait(done, 0, kDrainLimit);
+    }
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 

@@ -119,28 +119,12 @@ __device__ __forceinline__ uint32_t tile_pair(const uint64_t *tile_off, uint32_t
     return lo;
 }
 
-// Merge-path split of every merge tile's first diagonal, all tiles at once
-// (the kernel below then starts loading immediately).
-__global__ void k_isect_splits(uint32_t npairs, const lh_set *A, const lh_set *B, const PairPlan *plan,
-                               const uint64_t *tile_off, uint64_t *split) {
-    const uint64_t total = tile_off[npairs];
-    for (uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; tile < total;
-         tile += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = tile_pair(tile_off, npairs, tile);
-        const PairPlan pl = plan[p];
-        if (pl.kind != K_MERGE) continue;
-        lh_set a = A[p], b = B[p];
-        if (pl.swap) { lh_set x = a; a = b; b = x; }
-        split[tile] = mp_split(a.data, a.n, b.data, b.n, (tile - tile_off[p]) * kTile);
-    }
-}
-
-// split: per-tile merge-path starts from k_isect_splits, or null to compute
-// them here (the allocation-free entry point has no room for them)
+// Tile loop of the allocation-free entry point: every tile finds its pair and
+// its merge-path splits itself (no per-tile descriptors, which would need an
+// allocation sized by the tile count).
 __global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_set *A,
                                                     const lh_set *B, const PairPlan *plan,
-                                                    const uint64_t *tile_off, const uint64_t *split,
-                                                    uint64_t *counts) {
+                                                    const uint64_t *tile_off, uint64_t *counts) {
     __shared__ uint32_t sa[kTile];
     __shared__ uint32_t sb[kTile + 1];
     __shared__ uint64_t bounds[2];
@@ -149,7 +133,6 @@ __global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_se
     for (uint64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const uint32_t p = tile_pair(tile_off, npairs, tile);
         const uint64_t t = tile - tile_off[p];
-        const uint64_t ntp = tile_off[p + 1] - tile_off[p];
         const PairPlan pl = plan[p];
         lh_set a = A[p], b = B[p];
         if (pl.swap) { lh_set x = a; a = b; b = x; }
@@ -157,17 +140,10 @@ __global__ void __launch_bounds__(kThreads) k_isect(uint32_t npairs, const lh_se
         if (pl.kind == K_MERGE) {
             const uint64_t nd = a.n + b.n;
             const uint64_t d0 = t * kTile, d1 = min(nd, d0 + kTile);
-            uint64_t i0, i1;
-            if (split) {
-                i0 = split[tile];
-                i1 = (t + 1 < ntp) ? split[tile + 1] : a.n;
-            } else {
-                if (threadIdx.x == 0) bounds[0] = mp_split(a.data, a.n, b.data, b.n, d0);
-                else if (threadIdx.x == 32) bounds[1] = mp_split(a.data, a.n, b.data, b.n, d1);
-                __syncthreads();
-                i0 = bounds[0];
-                i1 = bounds[1];
-            }
+            if (threadIdx.x == 0) bounds[0] = mp_split(a.data, a.n, b.data, b.n, d0);
+            else if (threadIdx.x == 32) bounds[1] = mp_split(a.data, a.n, b.data, b.n, d1);
+            __syncthreads();
+            const uint64_t i0 = bounds[0], i1 = bounds[1];
             const uint64_t j0 = d0 - i0, j1 = d1 - i1;
             const uint32_t la = (uint32_t)(i1 - i0), lb = (uint32_t)(j1 - j0);
             const bool has_ext = j1 < b.n;
@@ -327,118 +303,6 @@ __global__ void k_isect_tiles(uint32_t npairs, const lh_set *A, const lh_set *B,
     }
 }
 
-__device__ __forceinline__ void prefetch_tile(const TileDesc &d, uint32_t (&ra)[kItems], uint32_t (&rb)[kItems + 1]) {
-    const uint32_t kind = d.kind & 255u;
-    if (kind == K_MERGE) {
-        const uint32_t lbx = d.lb + ((d.kind >> 8) & 1u);
-#pragma unroll
-        for (int r = 0; r < kItems; ++r) {
-            const uint32_t k = threadIdx.x + r * kThreads;
-            ra[r] = k < d.la ? __ldg(d.a + k) : 0u;
-            rb[r] = k < lbx ? __ldg(d.b + k) : 0u;
-        }
-        rb[kItems] = (threadIdx.x == 0 && (uint32_t)kTile < lbx) ? __ldg(d.b + kTile) : 0u;
-    } else if (kind == K_PROBE || kind == K_UBS) {
-#pragma unroll
-        for (int r = 0; r < kItems; ++r) {
-            const uint32_t k = threadIdx.x + r * kThreads;
-            ra[r] = k < d.la ? __ldg(d.a + k) : 0u;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_isect2(const TileDesc *desc, uint64_t total, uint64_t *counts) {
-    __shared__ uint32_t sa[kTile];
-    __shared__ uint32_t sb[kTile + 1];
-    __shared__ uint32_t red[kThreads / 32];
-    uint32_t ra[kItems], rb[kItems + 1];
-    uint64_t tile = blockIdx.x;
-    if (tile >= total) return;
-    TileDesc d = desc[tile];
-    prefetch_tile(d, ra, rb);
-    while (tile < total) {
-        const uint32_t kind = d.kind & 255u;
-        const bool has_ext = (d.kind >> 8) & 1u;
-        const uint32_t la = d.la, lb = d.lb, pair = d.pair;
-        uint32_t cnt = 0;
-        if (kind == K_MERGE) {
-            const uint32_t lbx = lb + (has_ext ? 1u : 0u);
-#pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const uint32_t k = threadIdx.x + r * kThreads;
-                if (k < la) sa[k] = ra[r];
-                if (k < lbx) sb[k] = rb[r];
-            }
-            if (threadIdx.x == 0 && (uint32_t)kTile < lbx) sb[kTile] = rb[kItems];
-        }
-        // the next tile's descriptor and data loads go out before this tile's work
-        uint32_t xa[kItems];
-#pragma unroll
-        for (int r = 0; r < kItems; ++r) xa[r] = ra[r];
-        const uint64_t next = tile + gridDim.x;
-        TileDesc nd = d;
-        if (next < total) {
-            nd = desc[next];
-            prefetch_tile(nd, ra, rb);
-        }
-        __syncthreads();
-        if (kind == K_MERGE) {
-            const uint32_t s = threadIdx.x * kItems;
-            const uint32_t e = min(s + kItems, la + lb);
-            if (s < e) {
-                uint32_t ii = sm_split(sa, la, sb, lb, s);
-                uint32_t jj = s - ii;
-                for (uint32_t step = s; step < e; ++step) {
-                    if (ii < la && (jj >= lb || sa[ii] <= sb[jj])) {
-                        const uint32_t av = sa[ii];
-                        const bool head = jj < lb || (jj == lb && has_ext);
-                        if (head && sb[jj] == av) ++cnt;
-                        ++ii;
-                    } else {
-                        ++jj;
-                    }
-                }
-            }
-        } else if (kind == K_UBS) {
-            uint32_t w[kItems];
-#pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const uint32_t k = threadIdx.x + r * kThreads;
-                const uint32_t dd = xa[r] - d.bbase;
-                const bool in = k < la && xa[r] >= d.bbase && (uint64_t)(dd >> 5) < d.bn;
-                w[r] = in ? __ldg(d.b + (dd >> 5)) : 0u;
-            }
-#pragma unroll
-            for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((xa[r] - d.bbase) & 31u)) & 1u;
-        } else if (kind == K_PROBE) {
-#pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const uint32_t k = threadIdx.x + r * kThreads;
-                if (k >= la) continue;
-                uint64_t l = 0, h = d.bn;
-                while (l < h) {
-                    const uint64_t m = (l + h) >> 1;
-                    if (__ldg(d.b + m) < xa[r]) l = m + 1;
-                    else h = m;
-                }
-                cnt += (l < d.bn && __ldg(d.b + l) == xa[r]) ? 1u : 0u;
-            }
-        } else if (kind == K_BB) {
-            const uint4 *pa = (const uint4 *)d.a;
-            const uint4 *pb = (const uint4 *)d.b;
-            const uint32_t nv = la >> 2;
-            for (uint32_t k = threadIdx.x; k < nv; k += kThreads) {
-                const uint4 x = __ldg(pa + k), y = __ldg(pb + k);
-                cnt += __popc(x.x & y.x) + __popc(x.y & y.y) + __popc(x.z & y.z) + __popc(x.w & y.w);
-            }
-        }
-        const uint32_t tot = block_sum(cnt, red);  // ends with a barrier: shared tiles are free again
-        if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + pair), (unsigned long long)tot);
-        tile = next;
-        d = nd;
-    }
-}
-
 // ---- TMA-staged merge tiles ------------------------------------------------
 // Merge slices are staged by cp.async.bulk (one copy per slice, issued by one
 // thread, completion on an mbarrier) into two shared buffers: the next tile's
@@ -450,6 +314,9 @@ __global__ void __launch_bounds__(kThreads) k_isect2(const TileDesc *desc, uint6
 
 constexpr uint32_t kBufA = kTile + 8, kBufB = kTile + 16;
 constexpr uint32_t kWaitLimit = 1u << 22;
+// Bound of the second wait after a timeout: copies already issued may still
+// land, so the block polls their phase this much longer before it exits.
+constexpr uint32_t kDrainLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -459,8 +326,8 @@ __device__ __forceinline__ void mbar_init1(uint64_t *bar) {
 __device__ __forceinline__ void mbar_arm(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -523,127 +390,6 @@ __device__ __forceinline__ void stage_merge(const TileDesc &d, uint32_t *sa, uin
     for (uint32_t k = b_from + threadIdx.x; k < lbx; k += kThreads) sb[offb + k] = __ldg(d.b + k);
 }
 
-__global__ void __launch_bounds__(kThreads) k_isect3(const TileDesc *desc, uint64_t total, uint64_t *counts,
-                                                     uint32_t *status) {
-    __shared__ __align__(128) uint32_t sa[2][kBufA];
-    __shared__ __align__(128) uint32_t sb[2][kBufB];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ uint32_t red[kThreads / 32];
-    uint64_t tile = blockIdx.x;
-    if (tile >= total) return;
-    if (threadIdx.x == 0) {
-        mbar_init1(&bar[0]);
-        mbar_init1(&bar[1]);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // merge tiles staged into each buffer so far, and the staged offsets
-    // (block-uniform values)
-    uint32_t uses0 = 0, uses1 = 0;
-    int offa0 = 0, offb0 = 0, offa1 = 0, offb1 = 0;
-    TileDesc d = desc[tile];
-    const uint64_t t1 = tile + gridDim.x;
-    TileDesc dn = d;
-    if (t1 < total) dn = desc[t1];
-    uint32_t buf = 0;
-    if ((d.kind & 255u) == K_MERGE) {
-        stage_merge(d, sa[0], sb[0], &bar[0], offa0, offb0);
-        uses0++;
-    }
-    while (tile < total) {
-        const uint64_t next = tile + gridDim.x;
-        const uint64_t next2 = next + gridDim.x;
-        TileDesc dnn = dn;
-        if (next2 < total) dnn = desc[next2];
-        const bool stage_next = next < total && (dn.kind & 255u) == K_MERGE;
-        // the next merge tile goes into the other buffer (free since the last barrier)
-        if (stage_next) {
-            if (buf == 0) { stage_merge(dn, sa[1], sb[1], &bar[1], offa1, offb1); uses1++; }
-            else { stage_merge(dn, sa[0], sb[0], &bar[0], offa0, offb0); uses0++; }
-        }
-        const uint32_t kind = d.kind & 255u;
-        const bool has_ext = (d.kind >> 8) & 1u;
-        const uint32_t la = d.la, lb = d.lb;
-        bool waited = true;
-        if (kind == K_MERGE) waited = mbar_wait_bounded(&bar[buf], ((buf ? uses1 : uses0) - 1) & 1u);
-        if (__syncthreads_or(!waited)) {
-            // a copy never landed: record it, let the other buffer's copy (if
-            // one was issued) land, and stop
-            if (threadIdx.x == 0) lh_set_status(status, LH_ETIMEOUT);
-            if (stage_next) mbar_wait_bounded(&bar[buf ^ 1], ((buf ? uses0 : uses1) - 1) & 1u);
-            __syncthreads();
-            break;
-        }
-        uint32_t cnt = 0;
-        const uint32_t *A = sa[buf] + (buf ? offa1 : offa0), *Bv = sb[buf] + (buf ? offb1 : offb0);
-        if (kind == K_MERGE) {
-            const uint32_t s = threadIdx.x * kItems;
-            const uint32_t e = min(s + kItems, la + lb);
-            if (s < e) {
-                uint32_t ii = sm_split(A, la, Bv, lb, s);
-                uint32_t jj = s - ii;
-                for (uint32_t step = s; step < e; ++step) {
-                    if (ii < la && (jj >= lb || A[ii] <= Bv[jj])) {
-                        const uint32_t av = A[ii];
-                        const bool head = jj < lb || (jj == lb && has_ext);
-                        if (head && Bv[jj] == av) ++cnt;
-                        ++ii;
-                    } else {
-                        ++jj;
-                    }
-                }
-            }
-        } else if (kind == K_UBS || kind == K_PROBE) {
-            uint32_t x[kItems];
-#pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const uint32_t k = threadIdx.x + r * kThreads;
-                x[r] = k < la ? __ldg(d.a + k) : 0u;
-            }
-            if (kind == K_UBS) {
-                uint32_t w[kItems];
-#pragma unroll
-                for (int r = 0; r < kItems; ++r) {
-                    const uint32_t k = threadIdx.x + r * kThreads;
-                    const uint32_t dd = x[r] - d.bbase;
-                    const bool in = k < la && x[r] >= d.bbase && (uint64_t)(dd >> 5) < d.bn;
-                    w[r] = in ? __ldg(d.b + (dd >> 5)) : 0u;
-                }
-#pragma unroll
-                for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((x[r] - d.bbase) & 31u)) & 1u;
-            } else {
-#pragma unroll
-                for (int r = 0; r < kItems; ++r) {
-                    const uint32_t k = threadIdx.x + r * kThreads;
-                    if (k >= la) continue;
-                    uint64_t l = 0, h = d.bn;
-                    while (l < h) {
-                        const uint64_t m = (l + h) >> 1;
-                        if (__ldg(d.b + m) < x[r]) l = m + 1;
-                        else h = m;
-                    }
-                    cnt += (l < d.bn && __ldg(d.b + l) == x[r]) ? 1u : 0u;
-                }
-            }
-        } else if (kind == K_BB) {
-            const uint4 *pa = (const uint4 *)d.a;
-            const uint4 *pb = (const uint4 *)d.b;
-            const uint32_t nv = la >> 2;
-            for (uint32_t k = threadIdx.x; k < nv; k += kThreads) {
-                const uint4 xx = __ldg(pa + k), yy = __ldg(pb + k);
-                cnt += __popc(xx.x & yy.x) + __popc(xx.y & yy.y) + __popc(xx.z & yy.z) + __popc(xx.w & yy.w);
-            }
-        }
-        const uint32_t tot = block_sum(cnt, red);  // ends with a barrier: this buffer is free again
-        if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + d.pair), (unsigned long long)tot);
-        // the next tile, if it is a merge tile, sits in the other buffer
-        if (stage_next) buf ^= 1;
-        tile = next;
-        d = dn;
-        dn = dnn;
-    }
-}
-
 // ---- merge tiles, version 4 --------------------------------------------------
 // One linear staging buffer filled by cp.async.bulk (the next tile's copies
 // overlap the current merge) and one padded copy of the current tile
@@ -702,8 +448,15 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
         bool waited = true;
         if (kind == K_MERGE) waited = mbar_wait_bounded(&bar, (uses - 1) & 1u);
         if (__syncthreads_or(!waited)) {
-            if (threadIdx.x == 0) lh_set_status(status, LH_ETIMEOUT);
-            break;
+            // the bulk copies of this tile may still land in shared memory:
+            // no new copy is issued, and thread 0 keeps polling the same
+            // phase with a much longer bound before the block may exit
+            if (threadIdx.x == 0) {
+                lh_set_status(status, LH_ETIMEOUT);
+                mbar_wait_bounded(&bar, (uses - 1) & 1u, kDrainLimit);
+            }
+            __syncthreads();
+            return;
         }
         if (kind == K_MERGE) {
             // linear staging -> padded copy with sentinels
@@ -785,8 +538,8 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
         d = dn;
         dn = dnn;
     }
-    // a staged tile that was not consumed (only after a timeout): let its copies land
-    __syncthreads();
+    // every staged tile was consumed (a tile is staged only when a later
+    // iteration exists to wait for it), so no copy is in flight here
 }
 
 }  // namespace
@@ -941,7 +694,7 @@ extern "C" lh_status lh_intersect_count_batch_noalloc(lh_ctx *ctx, uint32_t npai
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect, kThreads, 0);
     if (per_sm < 1) per_sm = 1;
     unsigned grid = (unsigned)(ctx->num_sms * per_sm);
-    LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, nullptr, counts));
+    LH_TRACED(ctx, "k_isect", k_isect<<<grid, kThreads, 0, ctx->stream>>>(npairs, a, b, plan, off, counts));
     LH_LAUNCH_CHECK();
     return LH_OK;
 }

@@ -110,6 +110,7 @@ struct ExpandOut {
     unsigned long long *count;   // COUNT without groups
     double *gsum;
     unsigned long long *gcount;
+    uint32_t *status;            // context status word (out-of-domain GROUP BY values)
 };
 
 template <int MODE>
@@ -206,14 +207,22 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
                     for (uint32_t p = 0; p < D.np; ++p)
                         if (D.e[p] == e) lp[e] = npos[p];
                 }
+                bool in_domain = true;
                 for (uint32_t k = 0; k < q.ngc; ++k) {
                     uint32_t gv;
                     if (q.g_is_key[k])
                         gv = (q.g_depth[k] == d) ? x : gvF[(uint64_t)q.g_slot[k] * capF + i];
                     else
                         gv = (uint32_t)__ldg(q.g_col[k] + lp[q.g_edge[k]]);
-                    if (gv >= q.g_card[k]) gv = q.g_card[k] - 1;  // out-of-domain values clamp
-                    g = g * q.g_card[k] + gv;
+                    // a value outside [0, card) (a negative int32 reads as a
+                    // huge unsigned value) breaks the caller's contract: the
+                    // tuple is left out and the error surfaces at the wait
+                    in_domain = in_domain && gv < q.g_card[k];
+                    g = g * q.g_card[k] + (gv < q.g_card[k] ? gv : 0u);
+                }
+                if (!in_domain) {
+                    lh_set_status(o.status, LH_EINVAL);
+                    ok = false;
                 }
                 if (!q.count_only) {
                     for (uint32_t e = 0; e < q.ne; ++e) {
@@ -324,6 +333,7 @@ struct Driver {
                 o.count = (unsigned long long *)r->d_count;
                 o.gsum = r->d_gsum;
                 o.gcount = (unsigned long long *)r->d_gcount;
+                o.status = ctx->d_status;
                 if (mode_last == M_COUNT)
                     LH_TRACED(ctx, "k_expand", k_expand<M_COUNT><<<grid_expand, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o));
                 else

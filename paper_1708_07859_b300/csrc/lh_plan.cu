@@ -165,6 +165,31 @@ static lh_status edge_cards(lh_ctx *ctx, const lh_query *q, const lh_relation_de
     return LH_OK;
 }
 
+extern "C" lh_status lh_plan_explain(lh_ctx *ctx, const lh_query *q, const uint32_t *order, int32_t *icost,
+                                     int64_t *weight, int64_t *cost) {
+    if (!ctx || !q || !order) return lh_fail(ctx, LH_EINVAL, "null argument");
+    if (q->n_attrs == 0 || q->n_attrs > LH_MAX_ATTRS || q->n_edges == 0 || q->n_edges > LH_MAX_EDGES)
+        return lh_fail(ctx, LH_EINVAL, "bad query sizes");
+    uint32_t seen = 0;
+    for (uint32_t i = 0; i < q->n_attrs; ++i) {
+        if (order[i] >= q->n_attrs || ((seen >> order[i]) & 1u)) return lh_fail(ctx, LH_EINVAL, "order is not a permutation");
+        seen |= 1u << order[i];
+    }
+    for (uint32_t e = 0; e < q->n_edges; ++e)
+        for (uint32_t c = 0; c < q->edges[e].nattrs; ++c)
+            if (q->edges[e].attrs[c] >= q->n_attrs) return lh_fail(ctx, LH_EINVAL, "edge %u: attribute out of range", e);
+    uint64_t cards[LH_MAX_EDGES];
+    LH_TRY(edge_cards(ctx, q, nullptr, cards));
+    int64_t w[LH_MAX_ATTRS] = {0};
+    lh_weights(q, cards, w);
+    for (uint32_t i = 0; i < q->n_attrs; ++i) {
+        if (icost) icost[i] = lh_icost_vertex(q, order, i);
+        if (weight) weight[i] = w[i];
+    }
+    if (cost) *cost = lh_cost_of(q, order, w);
+    return LH_OK;
+}
+
 extern "C" lh_status lh_plan(lh_ctx *ctx, const lh_query *q, lh_planner_kind kind, const lh_model *model,
                              const lh_relation_desc *const *rels, const lh_plan_opts *opts, lh_plan_t *out) {
     if (!ctx || !q || !out) return lh_fail(ctx, LH_EINVAL, "null argument");

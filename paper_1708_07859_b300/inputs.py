@@ -91,8 +91,11 @@ def chung_lu_edges(n: int, m: int, beta: float, seed: int):
         need = m - have
         k = k[:need]
         order_keys.append(k)
-        seen_keys = np.union1d(seen_keys, k)
         have += k.size
+        if have < m:
+            # k holds distinct keys none of which was seen: the union is the
+            # sorted concatenation
+            seen_keys = np.sort(np.concatenate([seen_keys, k]))
     keys = np.concatenate(order_keys)
     src = (keys // np.uint64(n)).astype(np.uint32)
     dst = (keys % np.uint64(n)).astype(np.uint32)
@@ -145,6 +148,37 @@ def batch_graph_sizes(count: int = 4096, seed_offset: int = 4):
 
 def batch_graph(i: int, n: int, m: int, seed_offset: int = 4):
     return gnm_edges(int(n), int(m), SEED_BASE + seed_offset + 1 + int(i))
+
+
+def _batch_graph_args(args):
+    return batch_graph(*args)
+
+
+def batch_graphs(count: int = 4096, seed_offset: int = 4, workers: int = 0):
+    """The ``count`` graphs of a batch (graph i is ``batch_graph(i, n_i,
+    m_i)``), drawn in parallel by a pool of fresh (spawned) worker processes
+    when ``workers`` != 1; every graph has its own seed, so the result does
+    not depend on the pool.  workers 0 = one per host core."""
+    ns, ms = batch_graph_sizes(count, seed_offset)
+    args = [(i, int(ns[i]), int(ms[i]), seed_offset) for i in range(count)]
+    import os
+    w = workers or (os.cpu_count() or 1)
+    if w <= 1 or count < 64:
+        return [batch_graph(*a) for a in args]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(w, 32)) as pool:
+        return pool.map(_batch_graph_args, args, chunksize=32)
+
+
+HUB_GRAPH = (1 << 20, 1 << 24, 2.1)   # n, m, degree exponent of the power-law batch graph
+
+
+def hub_graph(seed_offset: int = 4):
+    """The power-law graph that joins the uneven batch: Chung-Lu with 2^24
+    distinct edges over 2^20 vertices, degree exponent 2.1 (hub out-sets are
+    dense enough for the bitset layout)."""
+    n, m, beta = HUB_GRAPH
+    return chung_lu_edges(n, m, beta, SEED_BASE + seed_offset)
 
 
 # --------------------------------------------------------------------------

@@ -133,6 +133,7 @@ EXPORTS = {
     "lh_copy_h2d": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64],
     "lh_selftest_bounded_wait": [C.c_void_p, C.c_uint32],
     "lh_pool_reserve": [C.c_void_p, C.c_uint64],
+    "lh_pool_usage": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
     "lh_trace_enable": [C.c_void_p, C.c_int],
     "lh_trace_only": [C.c_void_p, C.c_char_p],
     "lh_trace_read": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
@@ -147,6 +148,7 @@ EXPORTS = {
     "lh_intersect_count_batch_noalloc": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_plan": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_edge_key_order": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
+    "lh_plan_explain": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_join_aggregate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_result_wait": [C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_result_free": [C.c_void_p, C.c_void_p],
@@ -243,6 +245,12 @@ class Context:
         """Map `nbytes` into the context's memory pool up front (lh_pool_reserve)."""
         self._check(lib().lh_pool_reserve(self.h, int(nbytes)))
 
+    def pool_usage(self, reset_high=False):
+        """(bytes in use now, high-water mark) of the context's pool (lh_pool_usage)."""
+        now, high = C.c_uint64(), C.c_uint64()
+        self._check(lib().lh_pool_usage(self.h, C.byref(now), C.byref(high), 1 if reset_high else 0))
+        return now.value, high.value
+
     def trace_only(self, name=None):
         """Time only kernels called `name` (None: every kernel); all are counted."""
         self._check(lib().lh_trace_only(self.h, name.encode() if name else None))
@@ -316,6 +324,17 @@ class Context:
         self._check(lib().lh_plan(self.h, C.byref(q), kind, model.h if model is not None else None,
                                   rel_arr, C.byref(opts) if opts is not None else None, C.byref(p)))
         return p
+
+    def plan_explain(self, q, order):
+        """Section 4 cost terms of `order`: (icost per position, weight per
+        attribute, total cost) -- lh_plan_explain."""
+        n = q.n_attrs
+        o = (C.c_uint32 * n)(*order)
+        ic = (C.c_int32 * n)()
+        w = (C.c_int64 * n)()
+        cost = C.c_int64()
+        self._check(lib().lh_plan_explain(self.h, C.byref(q), o, ic, w, C.byref(cost)))
+        return list(ic), list(w), cost.value
 
     def edge_key_order(self, q, plan, e):
         ko = (C.c_uint32 * MAX_LEVELS)()

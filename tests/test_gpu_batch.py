@@ -77,3 +77,40 @@ def test_batch_rejects_wrong_trie(ctx, lhlib):
     with pytest.raises(lh.LHError):
         lh.Batch(ctx, [(0, t)])
     t.free()
+
+
+@pytest.fixture(scope="module")
+def full_batch_graphs():
+    """The uneven batch at its stated size: 4096 G(n, m) graphs with
+    log-uniform edge counts 100..1e5 (even index: triangle, odd: 4-clique)
+    plus the 2^24-edge Chung-Lu graph (n = 2^20, exponent 2.1) as one more
+    triangle query."""
+    graphs = [(i % 2, g) for i, g in enumerate(gen.batch_graphs(4096))]
+    graphs.append((0, gen.hub_graph()))
+    return graphs
+
+
+def test_batch_full_size_vs_oracle(ctx, orc, lhlib, full_batch_graphs):
+    """Per-query counts of the 4097-query batch equal the oracle's; the hub
+    graph's triangles are counted by the oracle over the degree orientation,
+    a different route than the id-oriented join the GPU runs."""
+    lh = lhlib
+    graphs = full_batch_graphs
+    want = np.array([orc.triangle_count(s, d) if k == 0 else orc.clique4_count(s, d)
+                     for k, (s, d) in graphs[:-1]] + [orc.triangle_count_degree_ordered(*graphs[-1][1])],
+                    dtype=np.uint64)
+    tries, queries = make_batch(ctx, lh, graphs)
+    hub = tries[-1].stats()
+    assert hub.level_bs_sets[1] > 0          # hub out-sets took the bitset layout
+    tuning, _ = lh.batch_autotune(ctx, queries)
+    for tun in (None, tuning):
+        b = lh.Batch(ctx, queries, tun)
+        b.run()
+        got = b.result()
+        b.run()
+        again = b.result()
+        b.free()
+        assert np.array_equal(got, want), (tun, np.flatnonzero(got != want)[:10])
+        assert np.array_equal(again, want)
+    for t in tries:
+        t.free()

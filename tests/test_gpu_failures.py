@@ -59,3 +59,29 @@ def test_pool_reserve_and_refusal(ctx, orc, lhlib):
     g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), "triangle")
     assert g.run(lh.make_plan([0, 1, 2]))[0] == orc.triangle_count(s, d)
     g.free()
+
+
+@pytest.mark.parametrize("bad", [100, -1])
+def test_group_value_outside_its_domain_is_refused(ctx, orc, lhlib, bad):
+    """A GROUP BY value at or above its declared card (or a negative int32)
+    is reported as LH_EINVAL when the result is waited on, instead of being
+    merged into some group; the context keeps working."""
+    import torch
+    from helpers import dev
+    lh = lhlib
+    data = gen.star_schema(20_000, dims=(300, 80, 30, 5), seed=23)
+    data["d3_grp"] = data["d3_grp"].copy()
+    data["d3_grp"][int(data["k"][2][0])] = bad          # the first fact row's group leaves [0, 100)
+    keys = [dev_u32(k) for k in data["k"]]
+    sj = lh.StarJoin(ctx, keys, dev(data["price"]), dev(data["disc"]), dev(data["d3_grp"]),
+                     dev(data["d4_region"]))
+    t1 = ctx.filter_trie(dev(data["d1_date"]), 0, 10_000)
+    t2 = ctx.filter_trie(dev(data["d2_cat"]), 0, 100)
+    with pytest.raises(lh.LHError) as e:
+        sj.run(t1, t2)
+    assert e.value.status == lh.EINVAL
+    ctx.sync()
+    s, d = gen.gnm_edges(200, 1500, 3)
+    g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), "triangle")
+    assert g.run(lh.make_plan([0, 1, 2]))[0] == orc.triangle_count(s, d)
+    g.free(); t1.free(); t2.free(); sj.free()

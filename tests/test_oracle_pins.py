@@ -77,6 +77,32 @@ def test_graph_counts_match_brute_force(orc, seed, shape):
     assert orc.GRAPH_COUNT[shape](s, d) == bf
 
 
+def test_degree_ordered_triangles_closed_forms(orc):
+    for n in (3, 4, 9, 40):
+        assert orc.triangle_count_degree_ordered(*gen.complete_graph(n)) == C(n, 3)
+    assert orc.triangle_count_degree_ordered(*gen.complete_bipartite(6, 9)) == 0
+    assert orc.triangle_count_degree_ordered(*gen.cycle_graph(11)) == 0
+    assert orc.triangle_count_degree_ordered(*gen.wheel_graph(12)) == 12
+    s, d = gen.complete_graph(7)                       # duplicates and reversals
+    assert orc.triangle_count_degree_ordered(np.concatenate([s, d, s]), np.concatenate([d, s, d])) == C(7, 3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_degree_ordered_triangles_match_brute_force(orc, seed):
+    n = 14
+    s, d = gen.gnm_edges(n, 20 + 4 * seed, 5000 + seed)
+    rels, k = rels_for("triangle", s, d)
+    assert orc.triangle_count_degree_ordered(s, d) == orc.brute_force_count(k, rels, n)
+
+
+@pytest.mark.parametrize("beta", [2.1, 2.6])
+def test_degree_ordered_triangles_on_power_law_graphs(orc, beta):
+    """Hubs (low ids) make the id orientation and the degree orientation
+    differ the most; the counts agree."""
+    s, d = gen.chung_lu_edges(4000, 40000, beta, 17)
+    assert orc.triangle_count_degree_ordered(s, d) == orc.triangle_count(s, d) > 0
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_rst_join_with_distinct_relations(orc, seed):
     n = 12
