@@ -250,65 +250,245 @@ def algorithmic(kernel, n_rows, nnz_a, nnz_b, union, nnz_c):
 
 # ------------------------------------------- intersection micro-benchmark
 
-def intersect_fig4a(ctx, lh, hbm_peak, reps=5, seed_base=0):
+def _gap_sets(total_sets, card, gap, seed):
+    """``total_sets`` independent sorted sets of ``card`` values each with
+    Geometric(1/gap) gaps (a uniform random set of density ~1/gap), drawn as
+    slices of one long stream so hundreds of million-element sets are cheap."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(total_sets):
+        g = rng.geometric(1.0 / gap, size=card).astype(np.int64)
+        v = np.cumsum(g) - g[0]
+        out.append(v.astype(np.uint32))
+    return out
+
+
+def intersect_fig4a(ctx, lh, hbm_peak, l2, reps=5, seed_base=0):
     """Figure 4a shapes: batches of independent count-only intersections of
     equal-cardinality sets in the three layout pairings (density 1/2), plus
-    sparse uint sets (density 1/32).  Reports elements/s, algorithmic GB/s of
-    the k_isect launches (sets read once) and the fraction of HBM peak."""
+    sparse uint sets (density 1/32).  Every batch holds at least 4x the L2
+    (>= 504 MB of set data) and the 256 MB flush buffer is written between
+    repetitions, so each launch streams its sets from HBM.  Reports
+    elements/s, algorithmic GB/s of the k_isect launches (sets read once) and
+    the fraction of HBM peak."""
     import torch
-    from paper_1708_07859_b300 import inputs as gen
     out = {}
+    # name, card, gap, pairs, layouts (0 uint, 1 bitset)
     cases = [("uint_uint_sparse_1e6", 1_000_000, 32.0, 256, (0, 0)),
              ("uint_uint_1e6", 1_000_000, 2.0, 256, (0, 0)),
              ("uint_bs_1e6", 1_000_000, 2.0, 256, (0, 1)),
-             ("bs_bs_1e6", 1_000_000, 2.0, 256, (1, 1)),
+             ("bs_bs_1e6", 1_000_000, 2.0, 2048, (1, 1)),
              ("uint_uint_sparse_1e7", 10_000_000, 32.0, 32, (0, 0)),
-             ("bs_bs_1e7", 10_000_000, 2.0, 32, (1, 1))]
-    for name, card, gap, npairs, (la, lb) in cases:
-        keep, da, db = [], [], []
+             ("bs_bs_1e7", 10_000_000, 2.0, 256, (1, 1))]
+    for ci, (name, card, gap, npairs, (la, lb)) in enumerate(cases):
+        span = int(card * gap)
+        nw = (((span + 127) >> 7) << 2)             # words of a density-1/gap bitset over [0, span)
+        rng = np.random.Generator(np.random.PCG64(gen_seed(seed_base + ci)))
+        host_parts, descs = [], ([], [])
+        at = 0
         nbytes = 0
+        uint_sides = [side for side, lay in ((0, la), (1, lb)) if lay == 0]
+        sets = _gap_sets(len(uint_sides) * npairs, card, gap, gen_seed(seed_base + 100 + ci)) if uint_sides else []
+        si = 0
         for p in range(npairs):
             for side, lay in ((0, la), (1, lb)):
-                v = gen.gap_set(card, gap, gen.SEED_BASE + 900000 + seed_base + 2 * p + side)
                 if lay == 0:
-                    t = lh.to_device_u32(v)
-                    d = (0, 0, v.size, t.data_ptr())
-                    nbytes += 4 * v.size
+                    v = sets[si]
+                    si += 1
+                    data, d = v, (0, 0, v.size)
                 else:
-                    base = int(v[0]) & ~127
-                    nw = ((((int(v[-1]) - base) >> 5) + 1) + 3) & ~3
-                    dv = v.astype(np.int64) - base
-                    # distinct powers of two below 2^32 sum exactly in float64
-                    words = np.bincount(dv >> 5, weights=np.ldexp(1.0, (dv & 31).astype(np.int32)),
-                                        minlength=nw).astype(np.uint64).astype(np.uint32)
-                    t = lh.to_device_u32(words)
-                    d = (1, base, nw, t.data_ptr())
-                    nbytes += 4 * nw
-                keep.append(t)
-                (da if side == 0 else db).append(d)
-        A = torch.frombuffer(bytearray(lh.pack_sets(da)), dtype=torch.uint8).cuda()
-        B = torch.frombuffer(bytearray(lh.pack_sets(db)), dtype=torch.uint8).cuda()
+                    # a uniform random set of density 1/2 over [0, span) as a
+                    # bitset is a run of uniform random words
+                    data = rng.integers(0, 1 << 32, size=nw, dtype=np.uint64).astype(np.uint32)
+                    d = (1, 0, nw)
+                pad = (-data.size) % 4
+                host_parts.append(data)
+                if pad:
+                    host_parts.append(np.zeros(pad, np.uint32))
+                descs[side].append((*d, at))
+                at += data.size + pad
+                nbytes += 4 * data.size
+        buf = lh.to_device_u32(np.concatenate(host_parts))
+        del host_parts, sets
+        ptr = buf.data_ptr()
+        A = torch.frombuffer(bytearray(lh.pack_sets([(l, b, n, ptr + 4 * o) for l, b, n, o in descs[0]])),
+                             dtype=torch.uint8).cuda()
+        B = torch.frombuffer(bytearray(lh.pack_sets([(l, b, n, ptr + 4 * o) for l, b, n, o in descs[1]])),
+                             dtype=torch.uint8).cuda()
         counts = torch.zeros(npairs, dtype=torch.int64, device="cuda")
         ctx.intersect_count_batch(A, B, counts)
         torch.cuda.synchronize()
         ctx.trace_reset()
-        ctx.trace(True)
+        ctx.trace_only("k_isect")
         for _ in range(reps):
+            flush_l2(l2)
+            ctx.trace(True)
             ctx.intersect_count_batch(A, B, counts)
-        ctx.trace(False)
+            ctx.trace(False)
         tr = ctx.trace_read()
+        ctx.trace_only(None)
         n_l, tot = tr.get("k_isect", (0, 0.0))
         ms = tot / max(1, n_l)
-        elems = 2 * card * npairs
+        elems = 2 * card * npairs          # set cardinalities (a bitset of density 1/2 holds ~card values)
         gbs = nbytes / (ms / 1e3) / 1e9
-        out[name] = {"pairs": npairs, "card": card, "ms": ms, "gelem_s": elems / (ms / 1e3) / 1e9,
-                     "alg_bytes": nbytes, "gb_s": gbs, "frac_hbm": gbs / hbm_peak}
-        del keep, A, B, counts
+        out[name] = {"pairs": npairs, "card": card, "span": span, "set_bytes": nbytes, "ms": ms,
+                     "gelem_s": elems / (ms / 1e3) / 1e9, "gb_s": gbs, "frac_hbm": gbs / hbm_peak,
+                     "working_set_vs_l2": nbytes / (126 << 20), "l2_flushed_between_reps": True,
+                     "result_sum": int(counts.sum().item())}
+        del A, B, counts, buf
         torch.cuda.empty_cache()
     return out
 
 
-# ------------------------------------------------ planner and batched extras
+def gen_seed(k):
+    from paper_1708_07859_b300 import inputs as gen
+    return gen.SEED_BASE + 900000 + k
+
+
+# ------------------------------------------------ WCOJ extras (configs 1, 3, 4)
+
+def triangle_wcoj(ctx, lh, reps=50):
+    """The 3-way triangle join R(a,b) S(b,c) T(a,c) over G(4096, 32768),
+    order [a, b, c], COUNT: microseconds per join (lh_join_aggregate through
+    lh_result_wait, host round trips included) and input set elements per
+    second.  Its tries (~150 KB) live in L2, so the join is bound by launch
+    and round-trip latency: no HBM roofline applies."""
+    from paper_1708_07859_b300 import inputs as gen
+    s, d = gen.triangle_workload()
+    g = lh.GraphJoin(ctx, lh.to_device_u32(s), lh.to_device_u32(d), "triangle")
+    plan = lh.make_plan([0, 1, 2])
+    cnt, el = g.run(plan)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        g.run(plan)
+        ts.append(time.perf_counter() - t0)
+    g.free()
+    us = statistics.median(ts) * 1e6
+    return {"graph": {"n": 4096, "m": int(s.size)}, "count": cnt, "elements": el, "us_per_join": us,
+            "gelem_s": el / (us / 1e6) / 1e9, "roofline": "not meaningful (tries L2-resident; latency-bound)"}
+
+
+def star_join(ctx, lh, hbm_peak, sels=(0.01, 0.05, 0.2), reps=5):
+    """Star-schema join-aggregate at full size (60M fact rows): fact trie
+    build, then per D1 selectivity the two filter relations and the SUM ...
+    GROUP BY join, timed with CUDA events.  Algorithmic bytes of a join: 4 B
+    per set element its intersections examine, 8 B (the compensated fp32
+    price * (1 - discount) pair) per aggregated row, and the two filter
+    bitsets."""
+    import torch
+    from paper_1708_07859_b300 import inputs as gen
+    data = gen.star_schema()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    keys = [lh.to_device_u32(k) for k in data["k"]]
+    price, disc = dev(data["price"]), dev(data["disc"])
+    grp, reg = dev(data["d3_grp"]), dev(data["d4_region"])
+    d1, d2 = dev(data["d1_date"]), dev(data["d2_cat"])
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    torch.cuda.synchronize()
+    # the first build also pays one-time costs (kernel modules loaded on first
+    # use, pool growth); the second is the steady-state build time
+    e[4].record()
+    sj = lh.StarJoin(ctx, keys, price, disc, grp, reg)
+    e[5].record()
+    torch.cuda.synchronize()
+    sj.free()
+    e[0].record()
+    sj = lh.StarJoin(ctx, keys, price, disc, grp, reg)
+    e[1].record()
+    torch.cuda.synchronize()
+    out = {"fact_rows": int(data["price"].size), "trie_build_ms": e[0].elapsed_time(e[1]),
+           "trie_build_first_ms": e[4].elapsed_time(e[5]), "by_selectivity": {}}
+    for sel in sels:
+        f1, f2 = gen.date_range_for_selectivity(sel), (0, 7)
+        t1, t2 = ctx.filter_trie(d1, *f1), ctx.filter_trie(d2, *f2)
+        gs, gc, v = sj.run(t1, t2)                       # warm
+        torch.cuda.synchronize()
+        e[2].record()
+        for _ in range(reps):
+            gs, gc, v = sj.run(t1, t2)
+        e[3].record()
+        torch.cuda.synchronize()
+        join_ms = e[2].elapsed_time(e[3]) / reps
+        rows = int(gc.sum())
+        alg = 4 * int(v.elements) + 8 * rows + (gen.DIM_SIZES[0] + gen.DIM_SIZES[1]) // 8
+        gbs = alg / (join_ms / 1e3) / 1e9
+        out["by_selectivity"][str(sel)] = {
+            "groups": int((gc > 0).sum()), "rows_aggregated": rows, "elements": int(v.elements),
+            "join_ms": join_ms, "fact_rows_per_s": data["price"].size / (join_ms / 1e3),
+            "gelem_s": int(v.elements) / (join_ms / 1e3) / 1e9, "alg_bytes": alg, "alg_gb_s": gbs,
+            "frac_hbm": gbs / hbm_peak}
+        t1.free(); t2.free()
+    sj.free()
+    return out
+
+
+def batched_compare(ctx, lh, hbm_peak, l2, count=4096):
+    """The uneven batch at its stated size: 4096 triangle / 4-clique COUNT
+    queries over G(n, m) graphs with log-uniform 100..1e5 edges plus the
+    triangle query over the 2^24-edge Chung-Lu hub graph, in one persistent
+    graph-captured launch with autotuned thresholds (tuned on a held-out
+    sample of the batch), vs one lh_join_aggregate per query.  Reports the
+    replay time (L2 flushed before each), input set elements per second and
+    the algorithmic bytes of k_batch (every trie array read once)."""
+    import torch
+    from paper_1708_07859_b300 import inputs as gen
+    graphs = [(i % 2, g) for i, g in enumerate(gen.batch_graphs(count))]
+    graphs.append((0, gen.hub_graph()))
+    tries, queries = [], []
+    tbytes = 0
+    for kind, (s, d) in graphs:
+        t = ctx.build_trie([lh.to_device_u32(s), lh.to_device_u32(d)], key_order=[0, 1])
+        tries.append(t)
+        queries.append((kind, t))
+        tbytes += int(t.stats().device_bytes)
+    tuning, tune_ms = lh.batch_autotune(ctx, queries)
+    b = lh.Batch(ctx, queries, tuning)
+    b.run()
+    counts = b.result()
+    elems = b.elements()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for e0, e1 in ev:
+        flush_l2(l2)
+        e0.record()
+        b.run()
+        e1.record()
+    torch.cuda.synchronize()
+    batch_ms = statistics.median([a.elapsed_time(c) for a, c in ev])
+    # one lh_join_aggregate per query, on the same tries
+    seq = []
+    joins = []
+    for (kind, (s, d)), t in zip(graphs, tries):
+        j = lh.GraphJoin(ctx, None, None, "triangle" if kind == 0 else "clique4", card=int(s.size))
+        j.tries[((0, 1), (32, 32))] = t
+        joins.append(j)
+    plans = [lh.make_plan(list(range(j.n_attrs))) for j in joins]
+    for j, p in zip(joins[:64], plans[:64]):        # warm
+        j.run(p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j, p in zip(joins, plans):
+        seq.append(j.run(p)[0])
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3
+    same = bool(np.array_equal(np.asarray(seq, dtype=np.uint64), counts))
+    edges = int(sum(int(s.size) for _, (s, _) in graphs))
+    b.free()
+    for j in joins:
+        j.tries.clear()
+    for t in tries:
+        t.free()
+    gbs = tbytes / (batch_ms / 1e3) / 1e9
+    return {"queries": len(graphs), "edges": edges, "hub_graph": {"n": gen.HUB_GRAPH[0], "m": gen.HUB_GRAPH[1],
+                                                                  "beta": gen.HUB_GRAPH[2]},
+            "tuning": {"t_warp": tuning[0], "chunk": tuning[1], "ctas_per_sm": tuning[2]},
+            "batch_ms": batch_ms, "elements": elems, "gelem_s": elems / (batch_ms / 1e3) / 1e9,
+            "alg_bytes": tbytes, "alg_gb_s": gbs, "frac_hbm": gbs / hbm_peak,
+            "sequential_ms": seq_ms, "speedup": seq_ms / batch_ms, "identical_counts": same,
+            "edges_per_s_batch": edges / (batch_ms / 1e3)}
+
+
+# ------------------------------------------------ planner extras
 
 def planner_compare(ctx, lh, edges=1 << 20, n=1 << 17, seed_off=7):
     """Learned vs cost-model vs exhaustive-best plan times (ms, engine
@@ -325,99 +505,6 @@ def planner_compare(ctx, lh, edges=1 << 20, n=1 << 17, seed_off=7):
                                         "regret_cost", "learned_plan_s", "exhaustive_plan_s")}
     model.free()
     return out
-
-
-def star_join(ctx, lh, sel=0.05, reps=5):
-    """Star-schema join-aggregate at full size (60M fact rows): fact trie
-    build, the two filter relations, and the SUM ... GROUP BY join, timed
-    with CUDA events; fact rows per second over the join alone."""
-    import torch
-    from paper_1708_07859_b300 import inputs as gen
-    data = gen.star_schema()
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    keys = [lh.to_device_u32(k) for k in data["k"]]
-    price, disc = dev(data["price"]), dev(data["disc"])
-    grp, reg = dev(data["d3_grp"]), dev(data["d4_region"])
-    d1, d2 = dev(data["d1_date"]), dev(data["d2_cat"])
-    f1, f2 = gen.date_range_for_selectivity(sel), (0, 7)
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    torch.cuda.synchronize()
-    # the first build also pays one-time costs (kernel modules loaded on first
-    # use, pool growth); the second is the steady-state build time
-    e[4].record()
-    sj = lh.StarJoin(ctx, keys, price, disc, grp, reg)
-    e[5].record()
-    torch.cuda.synchronize()
-    sj.free()
-    e[0].record()
-    sj = lh.StarJoin(ctx, keys, price, disc, grp, reg)
-    e[1].record()
-    t1, t2 = ctx.filter_trie(d1, *f1), ctx.filter_trie(d2, *f2)
-    sj.run(t1, t2)                       # warm
-    torch.cuda.synchronize()
-    e[2].record()
-    for _ in range(reps):
-        gs, gc, _ = sj.run(t1, t2)
-    e[3].record()
-    torch.cuda.synchronize()
-    join_ms = e[2].elapsed_time(e[3]) / reps
-    out = {"fact_rows": int(data["price"].size), "selectivity_d1": sel, "groups": int((gc > 0).sum()),
-           "rows_aggregated": int(gc.sum()), "trie_build_ms": e[0].elapsed_time(e[1]),
-           "trie_build_first_ms": e[4].elapsed_time(e[5]), "join_ms": join_ms,
-           "fact_rows_per_s": data["price"].size / (join_ms / 1e3)}
-    t1.free(); t2.free(); sj.free()
-    return out
-
-
-def batched_compare(ctx, lh, count=1024):
-    """One persistent graph-captured launch over `count` triangle / 4-clique
-    COUNT queries (log-uniform 100..1e5 edges) vs one lh_join_aggregate per
-    query, with the autotuned thresholds."""
-    import torch
-    from paper_1708_07859_b300 import inputs as gen
-    ns, ms = gen.batch_graph_sizes(count)
-    graphs = [(i % 2, gen.batch_graph(i, ns[i], ms[i])) for i in range(count)]
-    tries, queries, joins = [], [], []
-    for kind, (s, d) in graphs:
-        ds, dd = lh.to_device_u32(s), lh.to_device_u32(d)
-        t = ctx.build_trie([ds, dd], key_order=[0, 1])
-        tries.append(t)
-        queries.append((kind, t))
-        joins.append(lh.GraphJoin(ctx, ds, dd, "triangle" if kind == 0 else "clique4"))
-    tuning, tune_ms = lh.batch_autotune(ctx, queries)
-    b = lh.Batch(ctx, queries, tuning)
-    b.run()
-    counts = b.result()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    reps = 5
-    for _ in range(reps):
-        b.run()
-    e1.record()
-    torch.cuda.synchronize()
-    batch_ms = e0.elapsed_time(e1) / reps
-    plans = [lh.make_plan(list(range(j.n_attrs))) for j in joins]
-    seq = []
-    for j, p in zip(joins, plans):       # warm the per-query tries
-        seq.append(j.run(p)[0])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for j, p in zip(joins, plans):
-        j.run(p)
-    torch.cuda.synchronize()
-    seq_ms = (time.perf_counter() - t0) * 1e3
-    same = bool(np.array_equal(np.asarray(seq, dtype=np.uint64), counts))
-    edges = int(sum(int(s.size) for _, (s, _) in graphs))
-    b.free()
-    for t in tries:
-        t.free()
-    for j in joins:
-        j.free()
-    return {"queries": count, "edges": edges, "tuning": {"t_warp": tuning[0], "chunk": tuning[1],
-                                                        "ctas_per_sm": tuning[2]},
-            "batch_ms": batch_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batch_ms,
-            "identical_counts": same, "edges_per_s_batch": edges / (batch_ms / 1e3)}
 
 
 def dram_traffic(kernel, rows):
@@ -511,6 +598,14 @@ def run_reference(args):
     return 0
 
 
+def wcoj_extras(ctx, lh, hbm, l2):
+    """The worst-case-optimal join paths themselves: the triangle join, the
+    star-schema join at three selectivities, the uneven batch at full size
+    and the planner comparison."""
+    return {"triangle": triangle_wcoj(ctx, lh), "star": star_join(ctx, lh, hbm),
+            "batched": batched_compare(ctx, lh, hbm, l2), "planner": planner_compare(ctx, lh)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -524,11 +619,12 @@ def main():
     from paper_1708_07859_b300 import lh
     if args.isect_only or args.extras_only:
         ctx = lh.Context()
+        l2 = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+        hbm = load_peaks()[0]
         if args.isect_only:
-            print(json.dumps({"intersect_fig4a": intersect_fig4a(ctx, lh, load_peaks()[0])}))
+            print(json.dumps({"intersect_fig4a": intersect_fig4a(ctx, lh, hbm, l2)}))
         else:
-            print(json.dumps({"planner": planner_compare(ctx, lh), "batched": batched_compare(ctx, lh),
-                              "star": star_join(ctx, lh)}))
+            print(json.dumps(wcoj_extras(ctx, lh, hbm, l2)))
         ctx.close()
         return 0
 
@@ -683,12 +779,10 @@ def main():
         e2e = {"value": all_elems / (e_total / 1e3) / 1e9, "unit": "Gelem/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_total / args.steps}
 
-    fig4a = None if args.no_isect else intersect_fig4a(ctx, lh, hbm_peak)
+    fig4a = None if args.no_isect else intersect_fig4a(ctx, lh, hbm_peak, l2)
     extras = {}
     if not args.no_extras and rank == 0:
-        extras["planner"] = planner_compare(ctx, lh)
-        extras["batched"] = batched_compare(ctx, lh)
-        extras["star"] = star_join(ctx, lh)
+        extras = wcoj_extras(ctx, lh, hbm_peak, l2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -36,6 +36,7 @@ extern "C" {
 #define LH_MAX_EDGES 8   /* relations of one query (hyperedges) */
 #define LH_MAX_ANNOS 4   /* annotation columns of one relation */
 #define LH_NFEAT 60      /* learned-planner feature vector length */
+#define LH_MAX_GROUP 6   /* GROUP BY columns of one query */
 
 typedef enum {
     LH_OK = 0,
@@ -285,7 +286,9 @@ typedef struct {
 /* A GROUP BY column: the int32 annotation column `anno` of edge `edge`'s trie
  * read at the edge's leaf position (a dimension attribute, Section 5 GROUP BY
  * annotation), or, with anno = -1, the value of key attribute `attr`.
- * Values must lie in [0, card). */
+ * card > 0 declares the domain: values must lie in [0, card) (a value
+ * outside it is reported as LH_EINVAL at the wait).  card = 0: the domain is
+ * unknown, any uint32 value; the query then groups through a hash table. */
 typedef struct {
     uint32_t edge;
     int32_t anno;
@@ -305,12 +308,40 @@ typedef struct {
     uint32_t n_edges;
     lh_edge edges[LH_MAX_EDGES];
     uint32_t semiring;          /* lh_semiring */
-    uint32_t n_group;           /* 0..2 */
-    lh_group group[2];
+    uint32_t n_group;           /* 0..LH_MAX_GROUP */
+    lh_group group[LH_MAX_GROUP];
     uint32_t materialized_mask; /* bit a: attribute a is an output (materialized) */
     uint32_t eq_selected_mask;  /* bit a: an equality selection touches attribute a */
     uint32_t exec;              /* lh_exec hint */
+    uint32_t group_impl;        /* lh_group_impl */
+    uint64_t group_capacity;    /* hash GROUP BY: slots of the shared table (0 = sized from the inputs) */
 } lh_query;
+
+/* How a GROUP BY on annotations (or keys) accumulates (Section 5).
+ *   LH_GROUP_AUTO: dense per-group arrays when at most two columns all
+ *     declare a card and the domain product is <= 2^26; otherwise the
+ *     paper's rule on the key tuple's width: at most three values -> private
+ *     tables, more -> the shared table.
+ *   LH_GROUP_DENSE: dense arrays (needs declared cards, product <= 2^26).
+ *   LH_GROUP_PRIVATE: every warp upserts into its own open-addressing table
+ *     in shared memory (the analog of the paper's per-thread hash maps; no
+ *     contention between warps); a full table spills into the shared table,
+ *     and each block merges its tables into it at the end.  Needs the packed
+ *     key (declared cards' bit widths, 32 bits per undeclared column) to fit
+ *     in 63 bits.
+ *   LH_GROUP_SHARED: one concurrent open-addressing table in device memory
+ *     (the analog of the paper's concurrent cuckoo map): slots claimed by
+ *     compare-and-swap on a 64-bit tag, the key tuple stored beside it, fp64
+ *     sums and uint64 counts added atomically.
+ * The hash paths report their groups as key tuples (lh_result_view
+ * group_keys); a shared table that fills up reports LH_EOVERFLOW at the
+ * wait. */
+typedef enum {
+    LH_GROUP_AUTO = 0,
+    LH_GROUP_DENSE = 1,
+    LH_GROUP_PRIVATE = 2,
+    LH_GROUP_SHARED = 3
+} lh_group_impl;
 
 /* --------------------------------------------------- planner (Section 4) */
 
@@ -390,13 +421,20 @@ typedef struct {
     const uint32_t *c_col;
     const float *c_val;
     uint64_t elements;          /* intersection input elements examined (probe count) */
+    /* hash GROUP BY (group_impl PRIVATE / SHARED): ngroups groups in no
+     * particular order; group g's key is group_keys[c * ngroups + g] for
+     * column c < n_group_cols; group_sum / group_count hold its totals */
+    uint32_t n_group_cols;
+    const uint32_t *group_keys;
+    uint32_t group_impl;        /* lh_group_impl the join used */
 } lh_result_view;
 
 /* Run query q under plan.  tries: host array of device tries, indexed by
  * edge.trie_slot; each edge's trie must have been built with the key order
  * lh_edge_key_order gives for this plan (checked: LH_EINVAL otherwise).
- * COUNT, SUM (compensated fp32, fp64 totals) and GROUP BY on up to two
- * columns are supported by the generic driver. */
+ * COUNT, SUM (compensated fp32, fp64 totals) and GROUP BY on up to
+ * LH_MAX_GROUP columns (dense arrays or hash tables, see lh_group_impl) are
+ * supported by the generic driver. */
 lh_status lh_join_aggregate(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
                             lh_trie *const *tries, lh_result **out);
 /* Wait for the result and fill `view` (host struct; device pointers inside;
@@ -417,6 +455,18 @@ lh_status lh_result_free(lh_ctx *ctx, lh_result *r);
  * otherwise).  Scratch: 4 bf16 copies of the inputs, from the stream's pool. */
 lh_status lh_dense_matmul(lh_ctx *ctx, const float *A, const float *B, int m, int n, int k,
                           float *c_bf16, double *c_refined);
+
+/* y = A x for a dense fp32 A (m x n, row-major) and x (n): the dense
+ * matrix-vector product attribute elimination leaves (Section 3.1: a single
+ * dense annotation in a flat, BLAS-compatible buffer; the DMV rows of
+ * Section 6.2 / Table 1).  Products are split error-free and summed as
+ * compensated fp32 pairs; y (fp32, m) receives the rounded sums and, when
+ * y_refined is not NULL, y_refined (fp64, m) the pairs' exact sums.  Any m,
+ * n >= 0; rows are read with 16-byte loads when n is a multiple of 4 and A
+ * and x are 16-byte aligned.  No scratch memory; asynchronous on the
+ * context stream. */
+lh_status lh_dense_matvec(lh_ctx *ctx, const float *A, const float *x, int m, int n, float *y,
+                          double *y_refined);
 
 /* --------------------------------- batched uneven joins (no paper counterpart) */
 
@@ -449,6 +499,10 @@ lh_status lh_batch_create(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs,
 /* Replay the captured graph on the context stream. */
 lh_status lh_batch_run(lh_ctx *ctx, lh_batch *b);
 lh_status lh_batch_free(lh_ctx *ctx, lh_batch *b);
+/* Input set elements of the intersections the last replay executed (for
+ * each intersection the cardinalities of every set taking part: the
+ * throughput measure of the join); waits for the stream. */
+lh_status lh_batch_elements(lh_ctx *ctx, lh_batch *b, uint64_t *elements);
 /* Sweep tunings (successive halving over a grid of t_warp, chunk and
  * ctas_per_sm) and return the fastest.  The candidates are timed on a fixed
  * sample of the batch -- every 4th query, or all of them when n < 8 -- so the

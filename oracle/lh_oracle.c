@@ -400,3 +400,31 @@ void orc_star_sum(uint64_t nfact, const uint32_t *k1, const uint32_t *k2, const 
     }
     free(part); free(pc);
 }
+
+/* Fact rows passing f1lo <= d1_date[k1] <= f1hi and f2lo <= d2_cat[k2] <=
+ * f2hi (pass[r] = 1) and every row's price * (1 - disc/100) in fp64: the
+ * selections and the aggregated expression of the star join, with no
+ * grouping (the caller forms key tuples). */
+void orc_star_pass(uint64_t nfact, const uint32_t *k1, const uint32_t *k2, const double *price,
+                   const int8_t *disc, const int32_t *d1_date, int32_t f1lo, int32_t f1hi,
+                   const int32_t *d2_cat, int32_t f2lo, int32_t f2hi, uint8_t *pass, double *val) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < (int64_t)nfact; ++r) {
+        int32_t dd = d1_date[k1[r]], cc = d2_cat[k2[r]];
+        pass[r] = (dd >= f1lo && dd <= f1hi && cc >= f2lo && cc <= f2hi) ? 1 : 0;
+        val[r] = price[r] * (1.0 - (double)disc[r] / 100.0);
+    }
+}
+
+/* Per-group Neumaier sums and counts of values v[i] in group gid[i]. */
+void orc_group_sum(uint64_t n, const uint64_t *gid, const double *v, uint64_t ngroups, double *sum,
+                   uint64_t *cnt) {
+    neu_t *acc = (neu_t *)calloc(ngroups ? ngroups : 1, sizeof(neu_t));
+    for (uint64_t g = 0; g < ngroups; ++g) cnt[g] = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        neu_add(&acc[gid[i]], v[i]);
+        cnt[gid[i]]++;
+    }
+    for (uint64_t g = 0; g < ngroups; ++g) sum[g] = neu_val(&acc[g]);
+    free(acc);
+}

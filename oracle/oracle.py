@@ -59,6 +59,10 @@ def lib():
         L.orc_star_sum.argtypes = [u64, u32p, u32p, u32p, u32p, u32p, u32p,
                                    u32p, i32, i32, u32p, i32, i32, u32p, u32p,
                                    ctypes.c_uint32, ctypes.c_uint32, u32p, u32p]
+        L.orc_star_pass.restype = None
+        L.orc_star_pass.argtypes = [u64, u32p, u32p, u32p, u32p, u32p, i32, i32, u32p, i32, i32, u32p, u32p]
+        L.orc_group_sum.restype = None
+        L.orc_group_sum.argtypes = [u64, u32p, u32p, u64, u32p, u32p]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -288,6 +292,14 @@ def dense_matmul(A, B):
     return A64 @ B64, np.abs(A64) @ np.abs(B64)
 
 
+def dense_matvec(A, x):
+    """y = A x in fp64 and the componentwise magnitude |A| |x| (the dense
+    matrix-vector product attribute elimination leaves, Section 3.1)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    x64 = np.asarray(x, dtype=np.float64)
+    return A64 @ x64, np.abs(A64) @ np.abs(x64)
+
+
 # ----------------------------------------------------------------- star join
 
 def star_sum(data, f1, f2, n_g1=100, n_g2=5, sample=None):
@@ -310,6 +322,35 @@ def star_sum(data, f1, f2, n_g1=100, n_g2=5, sample=None):
                        _p(d1), int(f1[0]), int(f1[1]), _p(d2), int(f2[0]), int(f2[1]),
                        _p(d3), _p(d4), n_g2, ng, _p(gs), _p(gc))
     return gs, gc
+
+
+def star_sum_keys(data, f1, f2, cols):
+    """SUM(price * (1 - discount)) and COUNT over the fact rows passing the
+    D1 date range f1 and D2 category range f2, GROUP BY the dimension
+    attributes ``cols`` = [(dimension index, column name), ...] (Section 5,
+    GROUP BY on annotations of any width).  Returns (keys (G x len(cols)
+    uint32, lexicographically sorted), sums fp64, counts): the distinct key
+    tuples of the passing rows (a sort), then a Neumaier sum per tuple."""
+    k = data["k"]
+    n = k[0].size
+    ks = [_u32(x) for x in k]
+    price = np.ascontiguousarray(data["price"], dtype=np.float64)
+    disc = np.ascontiguousarray(data["disc"], dtype=np.int8)
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    d1, d2 = i32(data["d1_date"]), i32(data["d2_cat"])
+    ok = np.zeros(n, dtype=np.uint8)
+    val = np.zeros(n, dtype=np.float64)
+    lib().orc_star_pass(n, _p(ks[0]), _p(ks[1]), _p(price), _p(disc), _p(d1), int(f1[0]), int(f1[1]),
+                        _p(d2), int(f2[0]), int(f2[1]), _p(ok), _p(val))
+    rows = np.flatnonzero(ok)
+    tup = np.stack([np.asarray(data[name])[ks[dim][rows]].astype(np.uint32) for dim, name in cols], axis=1)
+    keys, gid = np.unique(tup, axis=0, return_inverse=True)
+    gid = np.ascontiguousarray(gid.reshape(-1), dtype=np.uint64)
+    v = np.ascontiguousarray(val[rows])
+    sums = np.zeros(keys.shape[0], dtype=np.float64)
+    cnts = np.zeros(keys.shape[0], dtype=np.uint64)
+    lib().orc_group_sum(gid.size, _p(gid), _p(v), keys.shape[0], _p(sums), _p(cnts))
+    return keys.astype(np.uint32), sums, cnts
 
 
 # ------------------------------------------------- cost-based optimizer (Sec 4)

@@ -28,6 +28,7 @@ struct lh_batch {
     uint64_t *d_qoff = nullptr;        // first global vertex of each query (n + 1)
     uint64_t *d_item_off = nullptr;    // first item of each global vertex (V + 1)
     unsigned long long *d_ticket = nullptr;
+    unsigned long long *d_elems = nullptr;  // input set elements of every executed intersection
     uint64_t n_vertices = 0, n_items = 0;
     lh_batch_tuning tuning{};
     unsigned grid = 0;
@@ -74,7 +75,8 @@ __device__ __forceinline__ bool in_adj(const DTrie &T, uint32_t pu, uint32_t lo,
 __global__ void __launch_bounds__(kThreads) k_batch(const DTrie *tries, const uint64_t *qoff, uint32_t nq,
                                                     uint64_t V, const uint64_t *item_off, uint32_t t_warp,
                                                     uint32_t chunk, unsigned long long *ticket,
-                                                    unsigned long long *counts, const uint32_t *kinds) {
+                                                    unsigned long long *counts, const uint32_t *kinds,
+                                                    unsigned long long *elems) {
     __shared__ uint32_t cbuf[kWarps][kCBuf];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t n_items = item_off[V];
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const DTrie *tries, const ui
             e0 = a_lo + c * chunk;
             e1 = min(a_hi, e0 + chunk);
         }
-        unsigned long long local = 0;
+        unsigned long long local = 0, local_el = 0;  // local_el: warp-uniform
         for (uint32_t e = e0; e < e1; ++e) {
             const uint32_t b = __ldg(T.lv[1].vals + e);
             uint32_t pb;
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const DTrie *tries, const ui
             const bool walk_a = (a_hi - a_lo) <= (b_hi - b_lo);
             const uint32_t w_lo = walk_a ? a_lo : b_lo, w_hi = walk_a ? a_hi : b_hi;
             const uint32_t o_p = walk_a ? pb : pa, o_lo = walk_a ? b_lo : a_lo, o_hi = walk_a ? b_hi : a_hi;
+            local_el += (a_hi - a_lo) + (b_hi - b_lo);
             uint32_t nbuf = 0;
             for (uint32_t x0 = w_lo; x0 < w_hi; x0 += 32) {
                 const uint32_t x = x0 + lane;
@@ -130,6 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const DTrie *tries, const ui
                         uint32_t pc;
                         if (!lh_probe(T, 0, 0, 0, T.lv[0].n, c, &pc)) continue;
                         const uint32_t c_lo = __ldg(T.lv[0].offs + pc), c_hi = __ldg(T.lv[0].offs + pc + 1);
+                        local_el += (c_hi - c_lo) + (a_hi - a_lo) + (b_hi - b_lo);
                         for (uint32_t y = c_lo + lane; y < c_hi; y += 32) {
                             const uint32_t d = __ldg(T.lv[1].vals + y);
                             if (in_adj(T, pa, a_lo, a_hi, d) && in_adj(T, pb, b_lo, b_hi, d)) ++local;
@@ -143,6 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const DTrie *tries, const ui
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(LH_FULL, local, o);
         if (lane == 0 && local) atomicAdd(counts + q, local);
+        if (lane == 0 && local_el) atomicAdd(elems, local_el);
     }
 }
 
@@ -171,7 +176,7 @@ lh_status batch_build(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs, const l
     b->n_vertices = hq[n];
     auto fail = [&](lh_status st) {
         lh_free(ctx, b->d_tries); lh_free(ctx, b->d_kind); lh_free(ctx, b->d_qoff); lh_free(ctx, b->d_item_off);
-        lh_free(ctx, b->d_ticket);
+        lh_free(ctx, b->d_ticket); lh_free(ctx, b->d_elems);
         delete b;
         return st;
     };
@@ -181,6 +186,7 @@ lh_status batch_build(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs, const l
     if ((s = lh_alloc(ctx, &b->d_qoff, (size_t)n + 1)) != LH_OK) return fail(s);
     if ((s = lh_alloc(ctx, &b->d_item_off, b->n_vertices + 1)) != LH_OK) return fail(s);
     if ((s = lh_alloc(ctx, &b->d_ticket, 1)) != LH_OK) return fail(s);
+    if ((s = lh_alloc(ctx, &b->d_elems, 1)) != LH_OK) return fail(s);
     cudaMemcpyAsync(b->d_tries, ht.data(), n * sizeof(DTrie), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(b->d_kind, hk.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(b->d_qoff, hq.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream);
@@ -203,9 +209,10 @@ lh_status batch_build(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs, const l
     if (e == cudaSuccess) {
         cudaMemsetAsync(counts, 0, n * sizeof(uint64_t), b->cap_stream);
         cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned long long), b->cap_stream);
+        cudaMemsetAsync(b->d_elems, 0, sizeof(unsigned long long), b->cap_stream);
         k_batch<<<b->grid, kThreads, 0, b->cap_stream>>>(b->d_tries, b->d_qoff, n, b->n_vertices, b->d_item_off,
                                                              tun.t_warp, tun.chunk, b->d_ticket,
-                                                             (unsigned long long *)counts, b->d_kind);
+                                                             (unsigned long long *)counts, b->d_kind, b->d_elems);
         cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &b->graph);
         e = (e2 != cudaSuccess) ? e2 : cudaGetLastError();
     }
@@ -247,9 +254,14 @@ extern "C" lh_status lh_batch_free(lh_ctx *ctx, lh_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     lh_free(ctx, b->d_tries); lh_free(ctx, b->d_kind); lh_free(ctx, b->d_qoff); lh_free(ctx, b->d_item_off);
-    lh_free(ctx, b->d_ticket);
+    lh_free(ctx, b->d_ticket); lh_free(ctx, b->d_elems);
     delete b;
     return LH_OK;
+}
+
+extern "C" lh_status lh_batch_elements(lh_ctx *ctx, lh_batch *b, uint64_t *elements) {
+    if (!ctx || !b || !elements) return lh_fail(ctx, LH_EINVAL, "null argument");
+    return lh_readback(ctx, b->d_elems, sizeof(uint64_t), elements);
 }
 
 // Grid of tunings, successive halving: every candidate is timed once, the

@@ -265,6 +265,74 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ------------------------------------------------------------ matrix-vector
+
+// y = A x for a dense fp32 A (m x n, row-major): a matrix-vector product is
+// one pass over A with no reuse, so it is bound by HBM bandwidth, not by the
+// tensor cores.  One warp per row (rows strided over the grid), 16-byte
+// loads of A four deep per lane, x through the read-only cache; every
+// product is split error-free (TwoProduct) and summed as a compensated fp32
+// pair, then the lanes' pairs are combined by shuffles.
+constexpr int kDmvThreads = 256;
+constexpr int kDmvDepth = 4;
+
+template <bool VEC>
+__global__ void __launch_bounds__(kDmvThreads) k_dense_mv(const float *A, const float *x, int m, int n, float *y,
+                                                          double *y64) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * kDmvThreads + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * kDmvThreads) >> 5;
+    for (int r = warp; r < m; r += nwarps) {
+        const float *row = A + (size_t)r * n;
+        float sh = 0.f, sl = 0.f;
+        if (VEC) {
+            const float4 *a4 = (const float4 *)row;
+            const float4 *x4 = (const float4 *)x;
+            const int n4 = n >> 2;
+            int c = lane;
+            for (; c + 32 * (kDmvDepth - 1) < n4; c += 32 * kDmvDepth) {
+                float4 av[kDmvDepth], xv[kDmvDepth];
+#pragma unroll
+                for (int u = 0; u < kDmvDepth; ++u) {
+                    av[u] = __ldcs(a4 + c + 32 * u);  // streamed once: evict first
+                    xv[u] = __ldg(x4 + c + 32 * u);
+                }
+#pragma unroll
+                for (int u = 0; u < kDmvDepth; ++u) {
+                    float ph, pl;
+                    lh_two_prod(av[u].x, xv[u].x, ph, pl); lh_pair_add(sh, sl, ph, pl);
+                    lh_two_prod(av[u].y, xv[u].y, ph, pl); lh_pair_add(sh, sl, ph, pl);
+                    lh_two_prod(av[u].z, xv[u].z, ph, pl); lh_pair_add(sh, sl, ph, pl);
+                    lh_two_prod(av[u].w, xv[u].w, ph, pl); lh_pair_add(sh, sl, ph, pl);
+                }
+            }
+            for (; c < n4; c += 32) {
+                const float4 a = __ldcs(a4 + c), b = __ldg(x4 + c);
+                float ph, pl;
+                lh_two_prod(a.x, b.x, ph, pl); lh_pair_add(sh, sl, ph, pl);
+                lh_two_prod(a.y, b.y, ph, pl); lh_pair_add(sh, sl, ph, pl);
+                lh_two_prod(a.z, b.z, ph, pl); lh_pair_add(sh, sl, ph, pl);
+                lh_two_prod(a.w, b.w, ph, pl); lh_pair_add(sh, sl, ph, pl);
+            }
+        } else {
+            for (int c = lane; c < n; c += 32) {
+                float ph, pl;
+                lh_two_prod(__ldcs(row + c), __ldg(x + c), ph, pl);
+                lh_pair_add(sh, sl, ph, pl);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(LH_FULL, sh, o), ol = __shfl_xor_sync(LH_FULL, sl, o);
+            lh_pair_add(sh, sl, oh, ol);
+        }
+        if (lane == 0) {
+            y[r] = sh + sl;
+            if (y64) y64[r] = (double)sh + (double)sl;
+        }
+    }
+}
+
 // ------------------------------------------------------------ tensor maps
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -348,4 +416,24 @@ extern "C" lh_status lh_dense_matmul(lh_ctx *ctx, const float *A, const float *B
     lh_free(ctx, bh);
     lh_free(ctx, bl);
     return s;
+}
+
+extern "C" lh_status lh_dense_matvec(lh_ctx *ctx, const float *A, const float *x, int m, int n, float *y,
+                                     double *y_refined) {
+    if (!ctx) return LH_EINVAL;
+    if (!A || !x || !y) return lh_fail(ctx, LH_EINVAL, "null argument");
+    if (m < 0 || n < 0) return lh_fail(ctx, LH_EINVAL, "negative size");
+    if (m == 0) return LH_OK;
+    int per_sm = 0;
+    const bool vec = (n % 4) == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)x % 16) == 0;
+    if (vec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_mv<true>, kDmvThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_mv<false>, kDmvThreads, 0);
+    const unsigned grid = (unsigned)std::min<uint64_t>(lh_blocks((uint64_t)m * 32, kDmvThreads),
+                                                       (uint64_t)ctx->num_sms * std::max(1, per_sm));
+    if (vec)
+        LH_TRACED(ctx, "k_dense_mv", k_dense_mv<true><<<grid, kDmvThreads, 0, ctx->stream>>>(A, x, m, n, y, y_refined));
+    else
+        LH_TRACED(ctx, "k_dense_mv", k_dense_mv<false><<<grid, kDmvThreads, 0, ctx->stream>>>(A, x, m, n, y, y_refined));
+    LH_LAUNCH_CHECK();
+    return LH_OK;
 }

@@ -27,8 +27,26 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr uint32_t kSmemGroupsMax = 1024;
+constexpr int kMaxG = LH_MAX_GROUP;
+constexpr uint32_t kPrivSlots = 256;                 // per-warp private GROUP BY table
+constexpr unsigned long long kPrivEmpty = ~0ull;
+constexpr uint32_t kHashSpin = 1u << 20;             // bound of a wait on a slot being written
 
 enum { M_EMIT = 0, M_COUNT = 1, M_AGG = 2 };
+enum { G_DENSE = 0, G_PRIVATE = 1, G_SHARED = 2 };
+
+// Shared GROUP BY table (Section 5, the concurrent hash map): open
+// addressing over `cap` slots (a power of two).  tag 0 = empty; an even tag
+// (hash with the low bit clear) = claimed, key still being written; an odd
+// tag (the tuple's hash, low bit set) = key visible.  keys: ncol x cap,
+// column-major.
+struct HTab {
+    unsigned long long *tag;
+    uint32_t *keys;
+    double *sum;
+    unsigned long long *cnt;
+    uint32_t cap;
+};
 
 struct JEdge {
     DTrie t;
@@ -52,15 +70,103 @@ struct JQuery {
     JDepth D[LH_MAX_ATTRS];
     uint32_t nd;
     uint32_t ngc;                 // group columns
-    uint32_t g_is_key[2];         // 1: key attribute value, 0: int32 annotation column
-    uint32_t g_edge[2];
-    const int32_t *g_col[2];
-    uint32_t g_depth[2];          // depth that binds the key attribute
-    uint32_t g_slot[2];           // frontier slot of a key group value
-    uint32_t g_card[2];
-    uint32_t ngroups;             // 1 when no GROUP BY
+    uint32_t g_is_key[kMaxG];     // 1: key attribute value, 0: int32 annotation column
+    uint32_t g_edge[kMaxG];
+    const int32_t *g_col[kMaxG];
+    uint32_t g_depth[kMaxG];      // depth that binds the key attribute
+    uint32_t g_slot[kMaxG];       // frontier slot of a key group value
+    uint32_t g_card[kMaxG];       // 0 = undeclared domain (hash modes only)
+    uint32_t g_shift[kMaxG];      // private tables: bit offset of the column in the packed key
+    uint32_t ngroups;             // dense mode: groups (1 when no GROUP BY)
+    uint32_t gmode;               // G_DENSE, G_PRIVATE or G_SHARED
+    HTab ht;
     uint32_t count_only;          // COUNT semiring: no annotation product
 };
+
+// 64-bit finalizer of splitmix64 (Steele, Lea and Flood, 2014)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+// hash of a key tuple, odd (the ready tag of its slot)
+__device__ __forceinline__ unsigned long long tuple_hash(const uint32_t *kv, uint32_t n) {
+    unsigned long long h = 0x243f6a8885a308d3ull;
+    for (uint32_t k = 0; k < n; ++k) h = mix64(h ^ ((unsigned long long)kv[k] + ((unsigned long long)k << 32)));
+    return h | 1ull;
+}
+
+// Adds (v, c) to the group of key tuple kv in the shared table; false (and
+// the status word set) when the table is full or a slot stays claimed.
+__device__ bool ht_upsert(const HTab &H, uint32_t ncol, const uint32_t *kv, double v, unsigned long long c,
+                          uint32_t *status) {
+    const unsigned long long h = tuple_hash(kv, ncol), claimed = h & ~1ull;
+    uint32_t slot = (uint32_t)(h >> 20) & (H.cap - 1);
+    volatile unsigned long long *vtag = H.tag;
+    volatile uint32_t *vkeys = H.keys;
+    for (uint32_t probe = 0; probe < H.cap; ++probe) {
+        unsigned long long t = vtag[slot];
+        if (t == 0) {
+            const unsigned long long prev = atomicCAS(H.tag + slot, 0ull, claimed);
+            if (prev == 0) {
+                for (uint32_t k = 0; k < ncol; ++k) H.keys[(size_t)k * H.cap + slot] = kv[k];
+                __threadfence();
+                atomicExch(H.tag + slot, h);
+                atomicAdd(H.sum + slot, v);
+                atomicAdd(H.cnt + slot, c);
+                return true;
+            }
+            t = prev;
+        }
+        if ((t | 1ull) == h) {
+            for (uint32_t spin = 0; (t & 1ull) == 0; ++spin) {
+                if (spin >= kHashSpin) {
+                    lh_set_status(status, LH_ETIMEOUT);
+                    return false;
+                }
+                t = vtag[slot];
+            }
+            __threadfence();
+            bool eq = true;
+            for (uint32_t k = 0; k < ncol; ++k) eq = eq && vkeys[(size_t)k * H.cap + slot] == kv[k];
+            if (eq) {
+                atomicAdd(H.sum + slot, v);
+                atomicAdd(H.cnt + slot, c);
+                return true;
+            }
+        }
+        slot = (slot + 1) & (H.cap - 1);
+    }
+    lh_set_status(status, LH_EOVERFLOW);
+    return false;
+}
+
+__device__ __forceinline__ void unpack_key(const JQuery &q, unsigned long long K, uint32_t *kv) {
+    for (uint32_t k = 0; k < q.ngc; ++k) {
+        const uint32_t bits = (k + 1 < q.ngc ? q.g_shift[k + 1] : 64u) - q.g_shift[k];
+        const unsigned long long m = bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
+        kv[k] = (uint32_t)((K >> q.g_shift[k]) & m);
+    }
+}
+
+// Set slot flags and compaction of the shared table (at the wait).
+__global__ void k_ht_flags(const unsigned long long *tag, uint32_t cap, uint32_t *flag) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+        flag[i] = (tag[i] & 1ull) ? 1u : 0u;
+}
+__global__ void k_ht_scatter(HTab H, uint32_t ncol, const uint64_t *pos, uint64_t G, uint32_t *keys, double *sum,
+                             uint64_t *cnt) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < H.cap; i += gridDim.x * blockDim.x) {
+        if (!(H.tag[i] & 1ull)) continue;
+        const uint64_t g = pos[i];
+        for (uint32_t k = 0; k < ncol; ++k) keys[(size_t)k * G + g] = H.keys[(size_t)k * H.cap + i];
+        sum[g] = H.sum[i];
+        cnt[g] = H.cnt[i];
+    }
+}
 
 __device__ __forceinline__ uint32_t find_entry(const uint64_t *off, uint32_t nF, uint64_t c) {
     uint32_t lo = 0, hi = nF;  // off[lo] <= c < off[hi]
@@ -118,19 +224,36 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
                                                      const uint32_t *gvF, uint32_t nF, uint32_t capF,
                                                      const uint64_t *off, const uint8_t *drv,
                                                      uint64_t c0, uint64_t c1, ExpandOut o) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const JDepth &D = q.D[d];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
-    const bool use_smem = MODE == M_AGG && q.ngroups <= kSmemGroupsMax;
-    float2 *tab = (float2 *)smem;                                    // [nwarps][ngroups]
-    uint32_t *tcnt = (uint32_t *)(tab + (size_t)nwarps * q.ngroups);  // [nwarps][ngroups]
-    float *stage_h = (float *)(tcnt + (size_t)nwarps * q.ngroups);    // [nwarps][32]
+    const bool use_smem = MODE == M_AGG && q.gmode == G_DENSE && q.ngroups <= kSmemGroupsMax;
+    const bool use_priv = MODE == M_AGG && q.gmode == G_PRIVATE;
+    // dense:   float2 tab[nwarps][ngroups], uint32 tcnt[nwarps][ngroups], stage
+    // private: u64 pkey[nwarps][P], float phi, plo [nwarps][P], uint32 pcnt[nwarps][P], stage
+    float2 *tab = (float2 *)smem_raw;
+    uint32_t *tcnt = (uint32_t *)(tab + (use_smem ? (size_t)nwarps * q.ngroups : 0));
+    unsigned long long *pkey = (unsigned long long *)smem_raw;
+    float *phi = (float *)(pkey + (use_priv ? (size_t)nwarps * kPrivSlots : 0));
+    float *plo = phi + (use_priv ? (size_t)nwarps * kPrivSlots : 0);
+    uint32_t *pcnt = (uint32_t *)(plo + (use_priv ? (size_t)nwarps * kPrivSlots : 0));
+    float *stage_h = use_priv ? (float *)(pcnt + (size_t)nwarps * kPrivSlots)
+                              : (float *)(tcnt + (use_smem ? (size_t)nwarps * q.ngroups : 0));
     float *stage_l = stage_h + nwarps * 32;
     if (use_smem) {
         for (uint32_t k = threadIdx.x; k < nwarps * q.ngroups; k += blockDim.x) {
             tab[k] = make_float2(0.f, 0.f);
             tcnt[k] = 0;
+        }
+        __syncthreads();
+    }
+    if (use_priv) {
+        for (uint32_t k = threadIdx.x; k < nwarps * kPrivSlots; k += blockDim.x) {
+            pkey[k] = kPrivEmpty;
+            phi[k] = 0.f;
+            plo[k] = 0.f;
+            pcnt[k] = 0;
         }
         __syncthreads();
     }
@@ -199,6 +322,8 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
         } else {
             // leaf positions of every relation, the group and the product term
             uint32_t g = 0;
+            uint32_t kv[kMaxG];
+            unsigned long long K = kPrivEmpty;
             float th = 1.f, tl = 0.f;
             if (ok) {
                 uint32_t lp[LH_MAX_EDGES];
@@ -208,17 +333,22 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
                         if (D.e[p] == e) lp[e] = npos[p];
                 }
                 bool in_domain = true;
+                K = 0;
                 for (uint32_t k = 0; k < q.ngc; ++k) {
                     uint32_t gv;
                     if (q.g_is_key[k])
                         gv = (q.g_depth[k] == d) ? x : gvF[(uint64_t)q.g_slot[k] * capF + i];
                     else
                         gv = (uint32_t)__ldg(q.g_col[k] + lp[q.g_edge[k]]);
-                    // a value outside [0, card) (a negative int32 reads as a
-                    // huge unsigned value) breaks the caller's contract: the
-                    // tuple is left out and the error surfaces at the wait
-                    in_domain = in_domain && gv < q.g_card[k];
-                    g = g * q.g_card[k] + (gv < q.g_card[k] ? gv : 0u);
+                    // a value outside a declared [0, card) (a negative int32
+                    // reads as a huge unsigned value) breaks the caller's
+                    // contract: the tuple is left out and the error surfaces
+                    // at the wait
+                    const bool in = q.g_card[k] == 0 || gv < q.g_card[k];
+                    in_domain = in_domain && in;
+                    kv[k] = gv;
+                    g = g * q.g_card[k] + (in ? gv : 0u);
+                    K |= (unsigned long long)gv << q.g_shift[k];
                 }
                 if (!in_domain) {
                     lh_set_status(o.status, LH_EINVAL);
@@ -237,7 +367,47 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
                     }
                 }
             }
-            if (use_smem) {
+            if (use_priv) {
+                // lanes with one key tuple merge their terms; the leader
+                // upserts into this warp's table (claims by CAS, so two
+                // leaders never share a slot), spilling to the shared table
+                // when the warp's table is full
+                const unsigned long long key = ok ? K : kPrivEmpty;
+                const uint32_t peers = __match_any_sync(LH_FULL, key);
+                stage_h[warp * 32 + lane] = th;
+                stage_l[warp * 32 + lane] = tl;
+                __syncwarp();
+                if (ok && (peers & ((1u << lane) - 1u)) == 0) {
+                    float sh = 0.f, sl = 0.f;
+                    uint32_t m = peers;
+                    while (m) {
+                        const int s = __ffs(m) - 1;
+                        m &= m - 1;
+                        lh_pair_add(sh, sl, stage_h[warp * 32 + s], stage_l[warp * 32 + s]);
+                    }
+                    unsigned long long *wk = pkey + (size_t)warp * kPrivSlots;
+                    uint32_t slot = (uint32_t)mix64(K) & (kPrivSlots - 1);
+                    bool placed = false;
+                    for (uint32_t probe = 0; probe < kPrivSlots; ++probe) {
+                        const unsigned long long prev = atomicCAS(wk + slot, kPrivEmpty, K);
+                        if (prev == kPrivEmpty || prev == K) {
+                            const size_t c = (size_t)warp * kPrivSlots + slot;
+                            float ch = phi[c], cl = plo[c];
+                            lh_pair_add(ch, cl, sh, sl);
+                            phi[c] = ch;
+                            plo[c] = cl;
+                            pcnt[c] += __popc(peers);
+                            placed = true;
+                            break;
+                        }
+                        slot = (slot + 1) & (kPrivSlots - 1);
+                    }
+                    if (!placed) ht_upsert(q.ht, q.ngc, kv, (double)sh + (double)sl, __popc(peers), o.status);
+                }
+                __syncwarp();
+            } else if (MODE == M_AGG && q.gmode == G_SHARED) {
+                if (ok) ht_upsert(q.ht, q.ngc, kv, (double)th + (double)tl, 1ull, o.status);
+            } else if (use_smem) {
                 const uint32_t key = ok ? g : 0xFFFFFFFFu;
                 const uint32_t peers = __match_any_sync(LH_FULL, key);
                 stage_h[warp * 32 + lane] = th;
@@ -268,6 +438,17 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) my_count += __shfl_xor_sync(LH_FULL, my_count, s);
         if (lane == 0 && my_count) atomicAdd(o.count, (unsigned long long)my_count);
+    }
+    if (use_priv) {
+        // every warp merges its own table into the shared one
+        __syncwarp();
+        for (uint32_t sl = lane; sl < kPrivSlots; sl += 32) {
+            const size_t c = (size_t)warp * kPrivSlots + sl;
+            if (pkey[c] == kPrivEmpty) continue;
+            uint32_t kv[kMaxG];
+            unpack_key(q, pkey[c], kv);
+            ht_upsert(q.ht, q.ngc, kv, (double)phi[c] + (double)plo[c], pcnt[c], o.status);
+        }
     }
     if (use_smem) {
         __syncthreads();
@@ -484,13 +665,23 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
     jq.ngc = q->n_group;
     jq.ngroups = 1;
     dr.n_keygroups = 0;
-    if (q->n_group > 2) return lh_fail(ctx, LH_EUNSUPPORTED, "at most two GROUP BY columns");
+    if (q->n_group > kMaxG) return lh_fail(ctx, LH_EUNSUPPORTED, "at most %d GROUP BY columns", kMaxG);
+    bool all_cards = true;
+    uint64_t dense_groups = 1;
+    uint32_t packed_bits = 0;
+    uint64_t group_rows = 0;   // largest relation feeding a group column (sizes the shared table)
     for (uint32_t k = 0; k < q->n_group; ++k) {
         const lh_group &G = q->group[k];
-        if (G.card == 0) return lh_fail(ctx, LH_EINVAL, "group %u: card 0", k);
         jq.g_card[k] = G.card;
-        if ((uint64_t)jq.ngroups * G.card > (1ull << 26)) return lh_fail(ctx, LH_EUNSUPPORTED, "group domain above 2^26");
-        jq.ngroups *= G.card;
+        all_cards = all_cards && G.card > 0;
+        dense_groups = std::min<uint64_t>(dense_groups * std::max<uint32_t>(G.card, 1u), 1ull << 40);
+        jq.g_shift[k] = packed_bits;
+        uint32_t bits = 32;
+        if (G.card > 0) {
+            bits = 1;
+            while (bits < 32 && (1ull << bits) < G.card) ++bits;
+        }
+        packed_bits += bits;
         if (G.anno < 0) {
             jq.g_is_key[k] = 1;
             jq.g_slot[k] = dr.n_keygroups++;
@@ -498,6 +689,12 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
             for (uint32_t d = 0; d < plan->n_attrs; ++d)
                 if (plan->order[d] == G.attr) { jq.g_depth[k] = d; found = true; }
             if (!found) return lh_fail(ctx, LH_EINVAL, "group %u: attribute not in plan", k);
+            for (uint32_t e = 0; e < q->n_edges; ++e) {
+                const lh_edge &E = q->edges[e];
+                for (uint32_t c = 0; c < E.nattrs; ++c)
+                    if (E.attrs[c] == G.attr && E.trie_slot >= 0)
+                        group_rows = std::max<uint64_t>(group_rows, tries[E.trie_slot]->lv[E.nattrs - 1].n);
+            }
         } else {
             if (G.edge >= q->n_edges || q->edges[G.edge].trie_slot < 0) return lh_fail(ctx, LH_EINVAL, "group %u: bad edge", k);
             const lh_trie *t = tries[q->edges[G.edge].trie_slot];
@@ -505,8 +702,26 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
                 return lh_fail(ctx, LH_EINVAL, "group %u: needs an int32 annotation column", k);
             jq.g_edge[k] = G.edge;
             jq.g_col[k] = (const int32_t *)t->anno[G.anno];
+            group_rows = std::max<uint64_t>(group_rows, t->lv[t->nlevels - 1].n);
         }
     }
+    // implementation (Section 5): dense arrays for small declared domains,
+    // else private tables for key tuples of at most three values, the shared
+    // table for wider ones
+    uint32_t impl = q->group_impl;
+    const bool dense_ok = all_cards && q->n_group <= 2 && dense_groups <= (1ull << 26);
+    if (impl == LH_GROUP_AUTO)
+        impl = q->n_group == 0 || dense_ok ? LH_GROUP_DENSE : (q->n_group <= 3 && packed_bits <= 63) ? LH_GROUP_PRIVATE
+                                                                                                     : LH_GROUP_SHARED;
+    if (q->n_group == 0) impl = LH_GROUP_DENSE;
+    if (impl == LH_GROUP_DENSE && !dense_ok)
+        return lh_fail(ctx, LH_EUNSUPPORTED, "dense GROUP BY needs at most two columns with declared cards and a domain <= 2^26");
+    if (impl == LH_GROUP_PRIVATE && packed_bits > 63)
+        return lh_fail(ctx, LH_EUNSUPPORTED, "private GROUP BY tables need the packed key (%u bits) to fit 63 bits", packed_bits);
+    if (impl > LH_GROUP_SHARED) return lh_fail(ctx, LH_EINVAL, "unknown group_impl %u", impl);
+    jq.gmode = impl == LH_GROUP_DENSE ? G_DENSE : impl == LH_GROUP_PRIVATE ? G_PRIVATE : G_SHARED;
+    if (jq.gmode == G_DENSE) jq.ngroups = (uint32_t)dense_groups;
+    r->group_impl = impl;
     const bool is_count = q->semiring == LH_COUNT_U64;
     jq.count_only = is_count ? 1 : 0;
     const JDepth &DL = jq.D[jq.nd - 1];
@@ -517,9 +732,12 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
     dr.cap = 1u << 22;
     dr.smem_bytes = 0;
     int per_sm = 4;
-    if (dr.mode_last == M_AGG && jq.ngroups <= kSmemGroupsMax) {
-        dr.smem_bytes = (size_t)(kThreads / 32) * jq.ngroups * (sizeof(float2) + sizeof(uint32_t)) +
-                        (size_t)(kThreads / 32) * 32 * 2 * sizeof(float);
+    const size_t stage = (size_t)(kThreads / 32) * 32 * 2 * sizeof(float);
+    if (dr.mode_last == M_AGG && jq.gmode == G_DENSE && jq.ngroups <= kSmemGroupsMax)
+        dr.smem_bytes = (size_t)(kThreads / 32) * jq.ngroups * (sizeof(float2) + sizeof(uint32_t)) + stage;
+    else if (dr.mode_last == M_AGG && jq.gmode == G_PRIVATE)
+        dr.smem_bytes = (size_t)(kThreads / 32) * kPrivSlots * (8 + 4 + 4 + 4) + stage;
+    if (dr.smem_bytes) {
         cudaFuncSetAttribute(k_expand<M_AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dr.smem_bytes);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<M_AGG>, kThreads, dr.smem_bytes);
         if (per_sm < 1) per_sm = 1;
@@ -529,7 +747,7 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
     }
     dr.grid_expand = (unsigned)(ctx->num_sms * per_sm);
     // results
-    r->ngroups = (dr.mode_last == M_AGG) ? jq.ngroups : 0;
+    r->ngroups = (dr.mode_last == M_AGG && jq.gmode == G_DENSE) ? jq.ngroups : 0;
     LH_TRY(res_alloc(ctx, r, &r->d_count, 1));
     LH_TRY(res_alloc(ctx, r, &r->d_elems, 1));
     LH_CU(cudaMemsetAsync(r->d_count, 0, sizeof(uint64_t), ctx->stream));
@@ -539,6 +757,31 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
         LH_TRY(res_alloc(ctx, r, &r->d_gcount, r->ngroups));
         LH_CU(cudaMemsetAsync(r->d_gsum, 0, r->ngroups * sizeof(double), ctx->stream));
         LH_CU(cudaMemsetAsync(r->d_gcount, 0, r->ngroups * sizeof(uint64_t), ctx->stream));
+    }
+    if (dr.mode_last == M_AGG && jq.gmode != G_DENSE) {
+        // the shared table: twice the larger of the feeding relations' rows
+        // (clamped to [2^12, 2^24]) unless the query gives a capacity
+        uint64_t cap = q->group_capacity;
+        if (cap == 0) cap = std::min<uint64_t>(std::max<uint64_t>(2 * group_rows, 1ull << 12), 1ull << 24);
+        uint64_t c2 = 1;
+        while (c2 < cap) c2 <<= 1;
+        if (c2 > (1ull << 31)) return lh_fail(ctx, LH_EUNSUPPORTED, "group_capacity above 2^31");
+        HTab &H = jq.ht;
+        H.cap = (uint32_t)c2;
+        LH_TRY(res_alloc(ctx, r, &H.tag, c2));
+        LH_TRY(res_alloc(ctx, r, &H.keys, c2 * std::max<uint32_t>(1u, q->n_group)));
+        LH_TRY(res_alloc(ctx, r, &H.sum, c2));
+        LH_TRY(res_alloc(ctx, r, &H.cnt, c2));
+        LH_CU(cudaMemsetAsync(H.tag, 0, c2 * sizeof(unsigned long long), ctx->stream));
+        LH_CU(cudaMemsetAsync(H.sum, 0, c2 * sizeof(double), ctx->stream));
+        LH_CU(cudaMemsetAsync(H.cnt, 0, c2 * sizeof(unsigned long long), ctx->stream));
+        r->ht_tag = H.tag;
+        r->ht_keys = H.keys;
+        r->ht_sum = H.sum;
+        r->ht_cnt = H.cnt;
+        r->ht_cap = H.cap;
+        r->n_group_cols = q->n_group;
+        r->hash_pending = true;
     }
     // depth 0 starts from the single empty prefix
     return dr.run(0, nullptr, nullptr, 1, 1);
@@ -612,6 +855,36 @@ extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v
     LH_TRY(lh_sync(ctx));
     memset(v, 0, sizeof(*v));
     v->exec = r->exec;
+    if (r->hash_pending) {
+        // compact the shared GROUP BY table into dense group arrays (slot order)
+        r->hash_pending = false;
+        uint32_t *flag = nullptr;
+        uint64_t *pos = nullptr;
+        uint64_t G = 0;
+        lh_status s = lh_alloc(ctx, &flag, r->ht_cap);
+        if (s == LH_OK) s = lh_alloc(ctx, &pos, (size_t)r->ht_cap + 1);
+        if (s == LH_OK) {
+            const unsigned g = lh_blocks(r->ht_cap, 256, (unsigned)ctx->num_sms * 8);
+            LH_TRACED(ctx, "k_ht_flags", k_ht_flags<<<g, 256, 0, ctx->stream>>>(r->ht_tag, r->ht_cap, flag));
+            s = lh_scan_u32_to_u64(ctx, flag, pos, r->ht_cap);
+        }
+        if (s == LH_OK) s = lh_readback(ctx, pos + r->ht_cap, sizeof(uint64_t), &G);
+        if (s == LH_OK && G > 0xFFFFFFFFull) s = lh_fail(ctx, LH_EOVERFLOW, "too many groups");
+        if (s == LH_OK) s = res_alloc(ctx, r, &r->group_keys, std::max<uint64_t>(1, G * r->n_group_cols));
+        if (s == LH_OK) s = res_alloc(ctx, r, &r->d_gsum, std::max<uint64_t>(1, G));
+        if (s == LH_OK) s = res_alloc(ctx, r, &r->d_gcount, std::max<uint64_t>(1, G));
+        if (s == LH_OK && G) {
+            HTab H{r->ht_tag, r->ht_keys, r->ht_sum, (unsigned long long *)r->ht_cnt, r->ht_cap};
+            const unsigned g = lh_blocks(r->ht_cap, 256, (unsigned)ctx->num_sms * 8);
+            LH_TRACED(ctx, "k_ht_scatter", k_ht_scatter<<<g, 256, 0, ctx->stream>>>(H, r->n_group_cols, pos, G, r->group_keys,
+                                                                               r->d_gsum, r->d_gcount));
+        }
+        lh_free(ctx, flag);
+        lh_free(ctx, pos);
+        if (s == LH_OK) s = lh_sync(ctx);
+        if (s != LH_OK) return s;
+        r->ngroups = (uint32_t)G;
+    }
     uint64_t cnt = 0, el = 0;
     if (r->d_count) LH_CU(cudaMemcpy(&cnt, r->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
     if (r->d_elems) LH_CU(cudaMemcpy(&el, r->d_elems, sizeof(el), cudaMemcpyDeviceToHost));
@@ -629,6 +902,9 @@ extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v
         v->count = c;
     }
     v->ngroups = r->ngroups;
+    v->n_group_cols = r->group_keys ? r->n_group_cols : 0;
+    v->group_keys = r->group_keys;
+    v->group_impl = r->group_impl;
     v->group_sum = r->d_gsum;
     v->group_count = r->d_gcount;
     v->nrows = r->nrows;

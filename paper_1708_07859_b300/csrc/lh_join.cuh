@@ -19,6 +19,17 @@ struct lh_result {
     uint32_t *c_col = nullptr;
     float *c_val = nullptr;
     uint32_t semiring = 0;
+    // hash GROUP BY: the shared table (compacted into the group arrays at
+    // the wait) and the compacted keys
+    uint32_t group_impl = LH_GROUP_DENSE;
+    uint32_t n_group_cols = 0;
+    bool hash_pending = false;
+    unsigned long long *ht_tag = nullptr;
+    uint32_t *ht_keys = nullptr;
+    double *ht_sum = nullptr;
+    unsigned long long *ht_cnt = nullptr;
+    uint32_t ht_cap = 0;
+    uint32_t *group_keys = nullptr;
     std::vector<void *> allocs;
 };
 

@@ -22,6 +22,8 @@ MAX_ATTRS = 6
 MAX_EDGES = 8
 MAX_ANNOS = 4
 NFEAT = 60
+MAX_GROUP = 6
+GROUP_AUTO, GROUP_DENSE, GROUP_PRIVATE, GROUP_SHARED = 0, 1, 2, 3
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EOVERFLOW = range(7)
 COUNT_U64, SUM_F32_KAHAN, SUM_F64, SUMPROD_F32 = range(4)
@@ -82,9 +84,9 @@ class Group(C.Structure):
 
 class Query(C.Structure):
     _fields_ = [("n_attrs", C.c_uint32), ("n_edges", C.c_uint32), ("edges", Edge * MAX_EDGES),
-                ("semiring", C.c_uint32), ("n_group", C.c_uint32), ("group", Group * 2),
+                ("semiring", C.c_uint32), ("n_group", C.c_uint32), ("group", Group * MAX_GROUP),
                 ("materialized_mask", C.c_uint32), ("eq_selected_mask", C.c_uint32),
-                ("exec", C.c_uint32)]
+                ("exec", C.c_uint32), ("group_impl", C.c_uint32), ("group_capacity", C.c_uint64)]
 
 
 class Plan(C.Structure):
@@ -106,7 +108,8 @@ class ResultView(C.Structure):
                 ("ngroups", C.c_uint32), ("group_sum", C.c_void_p), ("group_count", C.c_void_p),
                 ("nrows", C.c_uint64), ("y", C.c_void_p), ("nnz", C.c_uint64), ("c_row", C.c_void_p),
                 ("c_off", C.c_void_p), ("c_col", C.c_void_p), ("c_val", C.c_void_p),
-                ("elements", C.c_uint64)]
+                ("elements", C.c_uint64), ("n_group_cols", C.c_uint32), ("group_keys", C.c_void_p),
+                ("group_impl", C.c_uint32)]
 
 
 class TraceEntry(C.Structure):
@@ -153,9 +156,11 @@ EXPORTS = {
     "lh_result_wait": [C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_result_free": [C.c_void_p, C.c_void_p],
     "lh_dense_matmul": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "lh_dense_matvec": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "lh_batch_create": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_batch_run": [C.c_void_p, C.c_void_p],
     "lh_batch_free": [C.c_void_p, C.c_void_p],
+    "lh_batch_elements": [C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_batch_autotune": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_model_create": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
     "lh_model_free": [C.c_void_p, C.c_void_p],
@@ -352,6 +357,12 @@ class Context:
         n = B.shape[1]
         self._check(lib().lh_dense_matmul(self.h, _ptr(A), _ptr(B), m, n, k, _ptr(c_bf16), _ptr(c_refined)))
 
+    def dense_matvec(self, A, x, y, y_refined=None):
+        """y = A x (dense fp32 A, m x n row-major); y_refined: optional fp64 output."""
+        m, n = A.shape
+        self._check(lib().lh_dense_matvec(self.h, _ptr(A), _ptr(x), int(m), int(n), _ptr(y),
+                                          _ptr(y_refined) if y_refined is not None else None))
+
 
 class Trie:
     def __init__(self, ctx, h, keep=()):
@@ -436,6 +447,14 @@ class Result:
         return (_dev_to_np(v.group_sum, v.ngroups, np.float64, self.ctx),
                 _dev_to_np(v.group_count, v.ngroups, np.uint64, self.ctx))
 
+    def group_keys(self):
+        """Hash GROUP BY: the groups' key tuples, shape (ngroups, n_group_cols)."""
+        v = self.view or self.wait()
+        if not v.n_group_cols:
+            return None
+        k = _dev_to_np(v.group_keys, v.ngroups * v.n_group_cols, np.uint32, self.ctx)
+        return k.reshape(v.n_group_cols, v.ngroups).T.copy()
+
     def y(self):
         v = self.view or self.wait()
         return _dev_to_np(v.y, v.nrows, np.float32, self.ctx)
@@ -454,7 +473,7 @@ class Result:
 # ----------------------------------------------------------------- queries
 
 def make_query(n_attrs, edges, semiring=COUNT_U64, group=(), materialized=(), eq_selected=(),
-               exec_hint=EXEC_AUTO):
+               exec_hint=EXEC_AUTO, group_impl=0, group_capacity=0):
     """edges: list of dicts {slot, attrs, anno=-1, flat=None (tensor), card=0};
     group: list of dicts {edge, anno=-1, attr=0, card}."""
     q = Query()
@@ -479,10 +498,12 @@ def make_query(n_attrs, edges, semiring=COUNT_U64, group=(), materialized=(), eq
         q.group[i].edge = g.get("edge", 0)
         q.group[i].anno = g.get("anno", -1)
         q.group[i].attr = g.get("attr", 0)
-        q.group[i].card = g["card"]
+        q.group[i].card = g.get("card", 0)
     q.materialized_mask = sum(1 << a for a in materialized)
     q.eq_selected_mask = sum(1 << a for a in eq_selected)
     q.exec = exec_hint
+    q.group_impl = group_impl
+    q.group_capacity = group_capacity
     return q
 
 
@@ -522,13 +543,13 @@ class GraphJoin:
     dst): each pattern edge is a hyperedge on E.  Tries of E are built in the
     key orders the plan needs (forward (src, dst) and reverse (dst, src))."""
 
-    def __init__(self, ctx, src_dev, dst_dev, shape, layout=(32, 32)):
+    def __init__(self, ctx, src_dev, dst_dev, shape, layout=(32, 32), card=None):
         self.ctx = ctx
         self.src, self.dst = src_dev, dst_dev
         self.n_attrs, self.pattern = GRAPH_SHAPES[shape]
         self.layout = layout
         self.tries = {}
-        card = int(src_dev.numel())
+        card = int(src_dev.numel()) if card is None else int(card)
         self.query = make_query(self.n_attrs, [{"slot": 0, "attrs": list(p), "card": card}
                                                for p in self.pattern])
 
@@ -596,12 +617,14 @@ class GraphJoin:
 class StarJoin:
     """Star-schema join-aggregate over Fact(k1..k4) with the annotation
     price * (1 - discount) (Section 3.1 rule 3), selections pushed into filter
-    relations on D1 and D2 (Section 3.2), GROUP BY two dimension attributes
-    reached through D3 and D4 (Section 5).  Attributes: k1=0, k2=1, k3=2,
-    k4=3."""
+    relations on D1 and D2 (Section 3.2), GROUP BY dimension attributes
+    reached through the dimension relations (Section 5).  Attributes: k1=0,
+    k2=1, k3=2, k4=3.  dim_cols: int32 dimension attribute per dimension
+    index (default {2: d3_grp, 3: d4_region}); each becomes a one-level
+    relation over its key whose annotation is the attribute."""
 
-    def __init__(self, ctx, keys, price, disc, d3_grp, d4_region, n_g1=100, n_g2=5,
-                 key_order=(0, 1, 2, 3), layout=None):
+    def __init__(self, ctx, keys, price, disc, d3_grp=None, d4_region=None, n_g1=100, n_g2=5,
+                 key_order=(0, 1, 2, 3), layout=None, dim_cols=None, dim_cards=None):
         import torch
         self.ctx = ctx
         self.n_g1, self.n_g2 = n_g1, n_g2
@@ -609,37 +632,60 @@ class StarJoin:
                                    annos=[(price, T_F64 if price.dtype == torch.float64 else T_F32),
                                           (disc, T_I8)],
                                    merge=MERGE_PRICE_DISCOUNT, layout=layout)
-        self.dims = []
-        for col in (d3_grp, d4_region):
+        cols = dict(dim_cols) if dim_cols else {}
+        if d3_grp is not None:
+            cols.setdefault(2, d3_grp)
+        if d4_region is not None:
+            cols.setdefault(3, d4_region)
+        self.cards = {2: n_g1, 3: n_g2}
+        self.cards.update(dim_cards or {})
+        self.dim = {}
+        for dim_i in sorted(cols):
+            col = cols[dim_i]
             ids = torch.arange(col.numel(), dtype=torch.int32, device=col.device)
-            self.dims.append(ctx.build_trie([ids], annos=[(col, T_I32)], merge=MERGE_FIRST, layout=layout))
+            self.dim[dim_i] = (ctx.build_trie([ids], annos=[(col, T_I32)], merge=MERGE_FIRST, layout=layout),
+                               int(col.numel()))
         self.nfact = int(keys[0].numel())
-        self.dim_sizes = [int(d3_grp.numel()), int(d4_region.numel())]
 
-    def query(self, order=(0, 1, 2, 3)):
+    def query(self, order=(0, 1, 2, 3), groups=(2, 3), group_impl=0, group_capacity=0, cards=True):
+        """groups: dimension indices whose attribute is a GROUP BY column, in
+        order; cards=False leaves their domains undeclared."""
         edges = [{"slot": 0, "attrs": [0, 1, 2, 3], "anno": 0, "card": self.nfact},
                  {"slot": 1, "attrs": [0], "card": 1},
-                 {"slot": 2, "attrs": [1], "card": 1},
-                 {"slot": 3, "attrs": [2], "card": self.dim_sizes[0]},
-                 {"slot": 4, "attrs": [3], "card": self.dim_sizes[1]}]
-        return make_query(4, edges, semiring=SUM_F32_KAHAN,
-                          group=[{"edge": 3, "anno": 0, "card": self.n_g1},
-                                 {"edge": 4, "anno": 0, "card": self.n_g2}])
+                 {"slot": 2, "attrs": [1], "card": 1}]
+        self.slots = [self.fact, None, None]
+        grp = []
+        for dim_i in groups:
+            t, n = self.dim[dim_i]
+            e = len(edges)
+            edges.append({"slot": e, "attrs": [dim_i], "card": n})
+            self.slots.append(t)
+            grp.append({"edge": e, "anno": 0, "card": self.cards.get(dim_i, 0) if cards else 0})
+        return make_query(4, edges, semiring=SUM_F32_KAHAN, group=grp, group_impl=group_impl,
+                          group_capacity=group_capacity)
 
-    def run(self, f1_trie, f2_trie, order=(0, 1, 2, 3)):
-        """Returns (group sums fp64, group counts, result view)."""
-        q = self.query(order)
+    def run(self, f1_trie, f2_trie, order=(0, 1, 2, 3), groups=(2, 3), group_impl=0, group_capacity=0,
+            cards=True, keys=False):
+        """Returns (group sums fp64, group counts, result view) -- plus the
+        group key tuples when keys=True (hash GROUP BY)."""
+        q = self.query(order, groups, group_impl, group_capacity, cards)
         plan = make_plan(list(order))
-        r = self.ctx.join_aggregate(q, plan, [self.fact, f1_trie, f2_trie] + self.dims)
-        v = r.wait()
-        gs, gc = r.groups()
-        r.free()
-        return gs, gc, v
+        tries = list(self.slots)
+        tries[1], tries[2] = f1_trie, f2_trie
+        r = self.ctx.join_aggregate(q, plan, tries)
+        try:
+            v = r.wait()
+            gs, gc = r.groups()
+            gk = r.group_keys() if keys else None
+        finally:
+            r.free()
+        return (gs, gc, v, gk) if keys else (gs, gc, v)
 
     def free(self):
         self.fact.free()
-        for d in self.dims:
-            d.free()
+        for t, _ in self.dim.values():
+            t.free()
+        self.dim = {}
 
 
 # ------------------------------------------------------ sparse LA helpers
@@ -691,6 +737,12 @@ class Batch:
     def result(self):
         self.ctx.sync()
         return self.counts.cpu().numpy().astype(np.uint64)
+
+    def elements(self):
+        """Input set elements of the last replay's intersections."""
+        el = C.c_uint64()
+        self.ctx._check(lib().lh_batch_elements(self.ctx.h, self.h, C.byref(el)))
+        return int(el.value)
 
     def free(self):
         if self.h:

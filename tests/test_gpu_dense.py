@@ -77,3 +77,36 @@ def test_dense_full_4096(ctx, orc, lhlib):
     c32, c64 = run(ctx, lhlib, A, B)
     r64, r32 = check(orc, A, B, c32, c64)
     print(f"dense 4096: max componentwise error / sum|ab|: bf16 {r32:.3e}, refined {r64:.3e}")
+
+
+# ------------------------------------------------------- dense matrix-vector
+
+def run_mv(ctx, A, x):
+    import torch
+    m, n = A.shape
+    dA, dx = torch.from_numpy(np.ascontiguousarray(A)).cuda(), torch.from_numpy(x).cuda()
+    y = torch.full((m,), float("nan"), dtype=torch.float32, device="cuda")
+    y64 = torch.full((m,), float("nan"), dtype=torch.float64, device="cuda")
+    ctx.dense_matvec(dA, dx, y, y64)
+    ctx.sync()
+    return y.cpu().numpy(), y64.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (37, 5), (512, 700), (1000, 4096), (333, 4100), (8192, 8192)])
+def test_dense_matvec_vs_oracle(ctx, orc, lhlib, shape):
+    """Componentwise |y - y64| <= 1e-6 * sum_j |a_ij x_j| (compensated fp32),
+    on row lengths that take the 16-byte path (n % 4 == 0) and the scalar one."""
+    m, n = shape
+    A = gen.dense_matrix(m, n, 70 + m)
+    x = gen.dense_vector(n, 71 + n)
+    y, y64 = run_mv(ctx, A, x)
+    w, wa = orc.dense_matvec(A, x)
+    assert np.all(np.abs(y.astype(np.float64) - w) <= 1e-6 * wa + 1e-30)
+    assert np.all(np.abs(y64 - w) <= 1e-6 * wa + 1e-30)
+
+
+def test_dense_matvec_identity_exact(ctx, lhlib):
+    n = 2048
+    x = gen.dense_vector(n, 9)
+    y, y64 = run_mv(ctx, np.eye(n, dtype=np.float32), x)
+    assert np.array_equal(y, x) and np.array_equal(y64, x.astype(np.float64))

@@ -245,6 +245,19 @@ def small_star(n=3000, seed=7):
     return gen.star_schema(n, dims=(400, 60, 30, 5), seed=seed)
 
 
+def test_dense_matvec_identity_and_small_integers(orc):
+    x = gen.dense_vector(37, 5)
+    y, ay = orc.dense_matvec(np.eye(37, dtype=np.float32), x)
+    assert np.array_equal(y, x.astype(np.float64)) and np.array_equal(ay, np.abs(x).astype(np.float64))
+    rng = np.random.default_rng(3)
+    A = rng.integers(-9, 10, size=(11, 13))
+    v = rng.integers(-9, 10, size=13)
+    y, ay = orc.dense_matvec(A, v)
+    for i in range(11):
+        assert y[i] == sum(int(A[i, j]) * int(v[j]) for j in range(13))
+        assert ay[i] == sum(abs(int(A[i, j]) * int(v[j])) for j in range(13))
+
+
 def test_star_all_pass_single_group_equals_direct_sum(orc):
     data = small_star()
     data = dict(data)
@@ -276,6 +289,46 @@ def test_star_brute_force_and_group_partition(orc):
     tot, _ = orc.star_sum(dict(data, d3_grp=np.zeros_like(data["d3_grp"]),
                                d4_region=np.zeros_like(data["d4_region"])), f1, f2)
     assert abs(tot[0] - math.fsum(gs.tolist())) <= 1e-9 * abs(tot[0])
+
+
+def test_star_sum_keys_partitions_like_the_dense_groups(orc):
+    """GROUP BY (d3_grp, d4_region) through the key-tuple route equals the
+    dense-group star_sum; wider tuples refine it (their sums add up to the
+    coarser groups' sums)."""
+    data = gen.star_schema(30_000, dims=(400, 90, 40, 5), seed=24)
+    f1, f2 = gen.date_range_for_selectivity(0.3), (0, 20)
+    ws, wc = orc.star_sum(data, f1, f2)
+    keys, sums, cnts = orc.star_sum_keys(data, f1, f2, [(2, "d3_grp"), (3, "d4_region")])
+    g = keys[:, 0].astype(np.int64) * 5 + keys[:, 1]
+    assert np.array_equal(cnts, wc[g]) and int(cnts.sum()) == int(wc.sum())
+    assert np.allclose(sums, ws[g], rtol=1e-12)
+    k4, s4, c4 = orc.star_sum_keys(data, f1, f2, [(0, "d1_seg"), (1, "d2_cat"), (2, "d3_grp"), (3, "d4_region")])
+    coarse = {}
+    for kk, ss, cc in zip(k4.tolist(), s4, c4):
+        a = coarse.setdefault((kk[2], kk[3]), [0.0, 0])
+        a[0] += ss
+        a[1] += int(cc)
+    for kk, ss, cc in zip(keys.tolist(), sums, cnts):
+        assert coarse[tuple(kk)][1] == int(cc) and math.isclose(coarse[tuple(kk)][0], ss, rel_tol=1e-12)
+
+
+def test_star_sum_keys_brute_force(orc):
+    data = gen.star_schema(400, dims=(50, 30, 20, 5), seed=25)
+    f1, f2 = (0, 1800), (3, 30)
+    cols = [(0, "d1_seg"), (1, "d2_cat"), (3, "d4_region")]
+    keys, sums, cnts = orc.star_sum_keys(data, f1, f2, cols)
+    want = {}
+    for r in range(400):
+        k1, k2 = int(data["k"][0][r]), int(data["k"][1][r])
+        if not (f1[0] <= data["d1_date"][k1] <= f1[1] and f2[0] <= data["d2_cat"][k2] <= f2[1]):
+            continue
+        t = tuple(int(data[name][int(data["k"][dim][r])]) for dim, name in cols)
+        a = want.setdefault(t, [0.0, 0])
+        a[0] += float(data["price"][r]) * (1.0 - int(data["disc"][r]) / 100.0)
+        a[1] += 1
+    assert sorted(want) == [tuple(x) for x in keys.tolist()]
+    for kk, ss, cc in zip(keys.tolist(), sums, cnts):
+        assert want[tuple(kk)][1] == int(cc) and math.isclose(want[tuple(kk)][0], ss, rel_tol=1e-12)
 
 
 def test_filter_keys_plain(orc):
