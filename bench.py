@@ -347,6 +347,37 @@ def gen_seed(k):
 
 # ------------------------------------------------ WCOJ extras (configs 1, 3, 4)
 
+def dense_mv(ctx, lh, hbm_peak, l2, n=16384, reps=10):
+    """y = A x for the dense 16384 x 16384 relation (the largest of the
+    paper's DMV sizes; A is 1 GiB), L2 flushed before each launch: kernel
+    time by events and algorithmic bytes (A, x read once, y written) over
+    the measured HBM peak."""
+    import torch
+    from paper_1708_07859_b300 import inputs as gen
+    A = torch.from_numpy(gen.dense_matrix(n, n, gen.SEED_BASE + 23)).cuda()
+    x = torch.from_numpy(gen.dense_vector(n, gen.SEED_BASE + 24)).cuda()
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    y64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.dense_matvec(A, x, y, y64)
+    torch.cuda.synchronize()
+    ctx.trace_reset()
+    ctx.trace_only("k_dense_mv")
+    for _ in range(reps):
+        flush_l2(l2)
+        ctx.trace(True)
+        ctx.dense_matvec(A, x, y, y64)
+        ctx.trace(False)
+    tr = ctx.trace_read()
+    ctx.trace_only(None)
+    nl, tot = tr.get("k_dense_mv", (0, 0.0))
+    ms = tot / max(1, nl)
+    alg = 4 * n * n + 4 * n + 4 * n + 8 * n
+    del A
+    torch.cuda.empty_cache()
+    return {"n": n, "ms": ms, "alg_bytes": alg, "gb_s": alg / (ms / 1e3) / 1e9,
+            "frac_hbm": alg / (ms / 1e3) / 1e9 / hbm_peak, "gflop_s": 2.0 * n * n / (ms / 1e3) / 1e9}
+
+
 def triangle_wcoj(ctx, lh, reps=50):
     """The 3-way triangle join R(a,b) S(b,c) T(a,c) over G(4096, 32768),
     order [a, b, c], COUNT: microseconds per join (lh_join_aggregate through
@@ -358,6 +389,10 @@ def triangle_wcoj(ctx, lh, reps=50):
     g = lh.GraphJoin(ctx, lh.to_device_u32(s), lh.to_device_u32(d), "triangle")
     plan = lh.make_plan([0, 1, 2])
     cnt, el = g.run(plan)
+    tries, q = g._bind(plan)
+    r = ctx.join_aggregate(q, plan, tries)
+    visited = int(r.wait().visited)
+    r.free()
     ts = []
     for _ in range(reps):
         t0 = time.perf_counter()
@@ -365,17 +400,20 @@ def triangle_wcoj(ctx, lh, reps=50):
         ts.append(time.perf_counter() - t0)
     g.free()
     us = statistics.median(ts) * 1e6
-    return {"graph": {"n": 4096, "m": int(s.size)}, "count": cnt, "elements": el, "us_per_join": us,
+    return {"graph": {"n": 4096, "m": int(s.size)}, "count": cnt, "elements": el, "visited": visited,
+            "us_per_join": us,
             "gelem_s": el / (us / 1e6) / 1e9, "roofline": "not meaningful (tries L2-resident; latency-bound)"}
 
 
 def star_join(ctx, lh, hbm_peak, sels=(0.01, 0.05, 0.2), reps=5):
     """Star-schema join-aggregate at full size (60M fact rows): fact trie
     build, then per D1 selectivity the two filter relations and the SUM ...
-    GROUP BY join, timed with CUDA events.  Algorithmic bytes of a join: 4 B
-    per set element its intersections examine, 8 B (the compensated fp32
-    price * (1 - discount) pair) per aggregated row, and the two filter
-    bitsets."""
+    GROUP BY join, timed with CUDA events.  gelem_s counts the input set
+    cardinalities of every intersection (bitset sets by cardinality).
+    Algorithmic bytes of a join: 4 B per set element its intersections read
+    (each candidate of the driving set and one probe into every other set:
+    the result view's `visited`), 8 B (the compensated fp32 price * (1 -
+    discount) pair) per aggregated row, and the two filter bitsets."""
     import torch
     from paper_1708_07859_b300 import inputs as gen
     data = gen.star_schema()
@@ -411,10 +449,11 @@ def star_join(ctx, lh, hbm_peak, sels=(0.01, 0.05, 0.2), reps=5):
         torch.cuda.synchronize()
         join_ms = e[2].elapsed_time(e[3]) / reps
         rows = int(gc.sum())
-        alg = 4 * int(v.elements) + 8 * rows + (gen.DIM_SIZES[0] + gen.DIM_SIZES[1]) // 8
+        alg = 4 * int(v.visited) + 8 * rows + (gen.DIM_SIZES[0] + gen.DIM_SIZES[1]) // 8
         gbs = alg / (join_ms / 1e3) / 1e9
         out["by_selectivity"][str(sel)] = {
             "groups": int((gc > 0).sum()), "rows_aggregated": rows, "elements": int(v.elements),
+            "visited": int(v.visited),
             "join_ms": join_ms, "fact_rows_per_s": data["price"].size / (join_ms / 1e3),
             "gelem_s": int(v.elements) / (join_ms / 1e3) / 1e9, "alg_bytes": alg, "alg_gb_s": gbs,
             "frac_hbm": gbs / hbm_peak}
@@ -486,6 +525,73 @@ def batched_compare(ctx, lh, hbm_peak, l2, count=4096):
             "alg_bytes": tbytes, "alg_gb_s": gbs, "frac_hbm": gbs / hbm_peak,
             "sequential_ms": seq_ms, "speedup": seq_ms / batch_ms, "identical_counts": same,
             "edges_per_s_batch": edges / (batch_ms / 1e3)}
+
+
+# ------------------------------------------------ multi-node GHD plans
+
+BI_QUERY = """SELECT n.n_name, SUM(f.price * (1 - f.disc / 100))
+FROM fact f, orders o, customer c, supplier s, nation n, region r
+WHERE f.f_order = o.o_key AND o.o_cust = c.c_key AND f.f_supp = s.s_key
+  AND c.c_nation = s.s_nation AND s.s_nation = n.n_key AND n.n_region = r.r_key
+  AND r.r_name = 2 AND o.o_date BETWEEN 700 AND 1064
+GROUP BY n.n_name"""
+
+
+def bi_catalog(lh, data):
+    import torch
+    z = data["sizes"]
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    u = lh.to_device_u32
+    ids = lambda n: torch.arange(n, dtype=torch.int32, device="cuda")
+    return {
+        "fact": {"keys": ["f_order", "f_supp"], "columns": ["price", "disc"], "rows": z["fact"],
+                 "data": {"f_order": u(data["fact_order"]), "f_supp": u(data["fact_supp"]),
+                          "price": to(data["price"]), "disc": to(data["disc"])}},
+        "orders": {"keys": ["o_key", "o_cust"], "columns": ["o_date"], "rows": z["orders"], "row_id_key": "o_key",
+                   "data": {"o_key": ids(z["orders"]), "o_cust": u(data["order_cust"]), "o_date": to(data["order_date"])}},
+        "customer": {"keys": ["c_key", "c_nation"], "rows": z["customer"], "row_id_key": "c_key",
+                     "data": {"c_key": ids(z["customer"]), "c_nation": u(data["cust_nation"])}},
+        "supplier": {"keys": ["s_key", "s_nation"], "rows": z["supplier"], "row_id_key": "s_key",
+                     "data": {"s_key": ids(z["supplier"]), "s_nation": u(data["supp_nation"])}},
+        "nation": {"keys": ["n_key", "n_region"], "columns": ["n_name"], "rows": z["nation"], "row_id_key": "n_key",
+                   "data": {"n_key": ids(z["nation"]), "n_region": u(data["nation_region"]),
+                            "n_name": to(data["nation_name"])}, "host": {"n_name": data["nation_name"]}},
+        "region": {"keys": ["r_key"], "columns": ["r_name"], "rows": z["region"], "row_id_key": "r_key",
+                   "data": {"r_key": ids(z["region"]), "r_name": to(data["region_name"])},
+                   "host": {"r_name": data["region_name"]}},
+    }
+
+
+def ghd_compare(ctx, lh, reps=3):
+    """The six-relation BI query (60M fact rows, 15M orders) from SQL text:
+    the chosen two-node GHD with its selections pushed into nodes of their
+    own, the same GHD with the selections kept in their nodes, and the whole
+    query as one node -- wall time per query (trie builds of the relations,
+    the nodes' joins and intermediate results, the final GROUP BY), with
+    identical groups required."""
+    from paper_1708_07859_b300 import inputs as gen
+    from paper_1708_07859_b300 import sql
+    data = gen.bi_schema()
+    cat = bi_catalog(lh, data)
+    out = {"rows": data["sizes"]}
+    ref = None
+    for name, kw in (("ghd_pushdown", {"pushdown": True}), ("ghd_in_node", {"pushdown": False}),
+                     ("one_node", {"pushdown": False, "single_node": True})):
+        sql.plan_and_run(ctx, BI_QUERY, cat, **kw)          # warm
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            res, tr, plan = sql.plan_and_run(ctx, BI_QUERY, cat, **kw)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        if ref is None:
+            ref = res
+        same = sorted(res) == sorted(ref) and all(res[k][1] == ref[k][1] and
+                                                  abs(res[k][0] - ref[k][0]) <= 1e-9 * abs(ref[k][0]) for k in res)
+        out[name] = {"ms": statistics.median(ts), "nodes": len(plan.nodes()), "fhw": plan.fhw,
+                     "groups": len(res), "same_groups": bool(same)}
+    out["pushdown_speedup"] = out["ghd_in_node"]["ms"] / out["ghd_pushdown"]["ms"]
+    out["vs_one_node"] = out["one_node"]["ms"] / out["ghd_pushdown"]["ms"]
+    return out
 
 
 # ------------------------------------------------ planner extras
@@ -603,7 +709,8 @@ def wcoj_extras(ctx, lh, hbm, l2):
     star-schema join at three selectivities, the uneven batch at full size
     and the planner comparison."""
     return {"triangle": triangle_wcoj(ctx, lh), "star": star_join(ctx, lh, hbm),
-            "batched": batched_compare(ctx, lh, hbm, l2), "planner": planner_compare(ctx, lh)}
+            "batched": batched_compare(ctx, lh, hbm, l2), "planner": planner_compare(ctx, lh),
+            "ghd": ghd_compare(ctx, lh), "dense_mv": dense_mv(ctx, lh, hbm, l2)}
 
 
 def main():

@@ -183,6 +183,24 @@ lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel, const uint32_t
 lh_status lh_filter_trie(lh_ctx *ctx, const int32_t *col, uint64_t n, int32_t lo, int32_t hi,
                          const lh_layout_policy *layout, lh_trie **out);
 
+/* A selection on a relation's rows: keep row r when lo <= col[r] <= hi
+ * (col: device int32, one value per row -- a key or an annotation of the
+ * relation, e.g. a date or a dictionary-encoded name). */
+typedef struct {
+    const int32_t *col;
+    int32_t lo, hi;
+} lh_row_filter;
+
+/* lh_build_trie over only the rows of `rel` that pass every filter of
+ * where[0 .. n_where) (0..4): the selection pushed below the joins into a
+ * GHD node of its own (Section 3.2), whose relation is the selected one.
+ * Compacts the passing rows (one readback of their count), then builds as
+ * lh_build_trie does.  Errors as lh_build_trie, plus LH_EINVAL for more than
+ * four filters or a null filter column. */
+lh_status lh_build_trie_where(lh_ctx *ctx, const lh_relation_desc *rel, const uint32_t *key_order,
+                              const lh_layout_policy *layout, lh_merge merge, const lh_row_filter *where,
+                              uint32_t n_where, lh_trie **out);
+
 lh_status lh_trie_free(lh_ctx *ctx, lh_trie *t);
 
 typedef struct {
@@ -314,7 +332,9 @@ typedef struct {
     uint32_t eq_selected_mask;  /* bit a: an equality selection touches attribute a */
     uint32_t exec;              /* lh_exec hint */
     uint32_t group_impl;        /* lh_group_impl */
-    uint64_t group_capacity;    /* hash GROUP BY: slots of the shared table (0 = sized from the inputs) */
+    uint64_t group_capacity;    /* hash GROUP BY: slots of the shared table (0 = twice the product of the
+                                   columns' domains -- declared cards, else the distinct values their
+                                   relations can hold -- clamped to [2^12, 2^24]) */
 } lh_query;
 
 /* How a GROUP BY on annotations (or keys) accumulates (Section 5).
@@ -427,6 +447,11 @@ typedef struct {
     uint32_t n_group_cols;
     const uint32_t *group_keys;
     uint32_t group_impl;        /* lh_group_impl the join used */
+    /* generic driver: set elements its intersections read -- every
+     * candidate of the smallest (driving) set plus one probe (a bitset word
+     * or a searched element) into each other set -- the data a count of
+     * `elements` boils down to when the larger sets are probed, not scanned */
+    uint64_t visited;
 } lh_result_view;
 
 /* Run query q under plan.  tries: host array of device tries, indexed by
@@ -437,6 +462,21 @@ typedef struct {
  * supported by the generic driver. */
 lh_status lh_join_aggregate(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
                             lh_trie *const *tries, lh_result **out);
+/* The result of q under plan as a relation of its own: one tuple per
+ * distinct value combination of the key attributes out_attrs[0 .. n_out)
+ * among the join results, annotated with the aggregate of the tuples under
+ * it -- the semiring sum of the annotation products (the number of join
+ * results for LH_COUNT_U64) -- as a compensated fp32 pair (annotation
+ * columns 0 and 1, f32 high and low parts, which a later join multiplies as
+ * one annotation).  This is the intermediate result an inner node of a GHD
+ * plan hands to its parent (Sections 2.3 and 3.2: the node's output is
+ * projected onto the attributes it shares with the parent, the others
+ * aggregated away).  The returned trie has levels in out_attrs order.
+ * Groups through the hash GROUP BY (group_impl AUTO picks private or shared
+ * tables); synchronises.  Errors as lh_join_aggregate and lh_build_trie. */
+lh_status lh_join_to_trie(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan, lh_trie *const *tries,
+                          uint32_t n_out, const uint32_t *out_attrs, const lh_layout_policy *layout,
+                          lh_trie **out);
 /* Wait for the result and fill `view` (host struct; device pointers inside;
  * for SPGEMM this is where nnz is read back). */
 lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *view);

@@ -428,3 +428,52 @@ void orc_group_sum(uint64_t n, const uint64_t *gid, const double *v, uint64_t ng
     for (uint64_t g = 0; g < ngroups; ++g) sum[g] = neu_val(&acc[g]);
     free(acc);
 }
+
+/* The six-relation BI query of the two-node GHD example (Section 3.1):
+ * SUM(price * (1 - disc/100)) over fact rows f joined with orders o
+ * (f.order = o), customer c (o.cust = c), supplier s (f.supp = s) where
+ * c.nation = s.nation = n, nation n's region r has name region_pick, and o's
+ * date lies in [dlo, dhi]; GROUP BY the nation's name.  A plain pairwise
+ * hash join: keys are row ids, so each lookup is an index.  gsum / gcnt are
+ * indexed by nation name (n_names entries). */
+void orc_bi_q5(uint64_t nfact, const uint32_t *f_order, const uint32_t *f_supp, const double *price,
+               const int8_t *disc, const uint32_t *o_cust, const int32_t *o_date, const uint32_t *c_nation,
+               const uint32_t *s_nation, const uint32_t *n_region, const int32_t *n_name,
+               const int32_t *r_name, int32_t region_pick, int32_t dlo, int32_t dhi, uint32_t n_names,
+               double *gsum, uint64_t *gcnt) {
+    int nt = orc_num_threads();
+    neu_t *part = (neu_t *)calloc((size_t)nt * n_names, sizeof(neu_t));
+    uint64_t *pc = (uint64_t *)calloc((size_t)nt * n_names, sizeof(uint64_t));
+    #pragma omp parallel
+    {
+#ifdef _OPENMP
+        int t = omp_get_thread_num();
+#else
+        int t = 0;
+#endif
+        #pragma omp for schedule(static)
+        for (int64_t r = 0; r < (int64_t)nfact; ++r) {
+            uint32_t o = f_order[r];
+            int32_t d = o_date[o];
+            if (d < dlo || d > dhi) continue;
+            uint32_t n = c_nation[o_cust[o]];
+            if (n != s_nation[f_supp[r]]) continue;
+            if (r_name[n_region[n]] != region_pick) continue;
+            uint32_t g = (uint32_t)n_name[n];
+            neu_add(&part[(size_t)t * n_names + g], price[r] * (1.0 - (double)disc[r] / 100.0));
+            pc[(size_t)t * n_names + g]++;
+        }
+    }
+    for (uint32_t g = 0; g < n_names; ++g) {
+        neu_t a = {0, 0};
+        uint64_t c = 0;
+        for (int t = 0; t < nt; ++t) {
+            neu_add(&a, part[(size_t)t * n_names + g].s);
+            neu_add(&a, part[(size_t)t * n_names + g].c);
+            c += pc[(size_t)t * n_names + g];
+        }
+        gsum[g] = neu_val(&a);
+        gcnt[g] = c;
+    }
+    free(part); free(pc);
+}

@@ -63,6 +63,8 @@ def lib():
         L.orc_star_pass.argtypes = [u64, u32p, u32p, u32p, u32p, u32p, i32, i32, u32p, i32, i32, u32p, u32p]
         L.orc_group_sum.restype = None
         L.orc_group_sum.argtypes = [u64, u32p, u32p, u64, u32p, u32p]
+        L.orc_bi_q5.restype = None
+        L.orc_bi_q5.argtypes = [u64] + [u32p] * 11 + [i32, i32, i32, ctypes.c_uint32, u32p, u32p]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -351,6 +353,26 @@ def star_sum_keys(data, f1, f2, cols):
     cnts = np.zeros(keys.shape[0], dtype=np.uint64)
     lib().orc_group_sum(gid.size, _p(gid), _p(v), keys.shape[0], _p(sums), _p(cnts))
     return keys.astype(np.uint32), sums, cnts
+
+
+def bi_q5(data, region_pick, dates):
+    """Per nation name: SUM(price * (1 - discount)) and COUNT of the
+    six-relation BI join (fact, orders, customer, supplier, nation, region)
+    with customer and supplier in one nation, the nation's region named
+    ``region_pick`` and the order date in ``dates`` = [lo, hi] (Sections 2.3,
+    3.1).  A pairwise hash join over row-id keys."""
+    c = lambda a, t: np.ascontiguousarray(a, dtype=t)
+    u, i = np.uint32, np.int32
+    nn = int(data["nation_name"].max()) + 1
+    gs = np.zeros(nn, dtype=np.float64)
+    gc = np.zeros(nn, dtype=np.uint64)
+    args = [c(data["fact_order"], u), c(data["fact_supp"], u), c(data["price"], np.float64),
+            c(data["disc"], np.int8), c(data["order_cust"], u), c(data["order_date"], i),
+            c(data["cust_nation"], u), c(data["supp_nation"], u), c(data["nation_region"], u),
+            c(data["nation_name"], i), c(data["region_name"], i)]
+    lib().orc_bi_q5(args[0].size, *[_p(a) for a in args], int(region_pick), int(dates[0]), int(dates[1]),
+                    nn, _p(gs), _p(gc))
+    return gs, gc
 
 
 # ------------------------------------------------- cost-based optimizer (Sec 4)

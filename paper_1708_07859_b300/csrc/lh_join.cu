@@ -506,6 +506,7 @@ struct Driver {
         }
         if (s == LH_OK) s = lh_readback(ctx, off + nF, sizeof(uint64_t), &total);
         const bool last = d + 1 == q.nd;
+        if (s == LH_OK && !(last && shortcut_last)) r->visited += total * q.D[d].np;
         if (s == LH_OK && last) {
             if (shortcut_last) {
                 r->host_count += total;
@@ -669,7 +670,7 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
     bool all_cards = true;
     uint64_t dense_groups = 1;
     uint32_t packed_bits = 0;
-    uint64_t group_rows = 0;   // largest relation feeding a group column (sizes the shared table)
+    uint64_t group_space = 1;  // bound on the distinct key tuples (sizes the shared table)
     for (uint32_t k = 0; k < q->n_group; ++k) {
         const lh_group &G = q->group[k];
         jq.g_card[k] = G.card;
@@ -689,12 +690,18 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
             for (uint32_t d = 0; d < plan->n_attrs; ++d)
                 if (plan->order[d] == G.attr) { jq.g_depth[k] = d; found = true; }
             if (!found) return lh_fail(ctx, LH_EINVAL, "group %u: attribute not in plan", k);
+            // distinct values of a key attribute: at most the smallest level
+            // holding it among the relations that contain it
+            uint64_t dom = UINT64_MAX;
             for (uint32_t e = 0; e < q->n_edges; ++e) {
                 const lh_edge &E = q->edges[e];
-                for (uint32_t c = 0; c < E.nattrs; ++c)
-                    if (E.attrs[c] == G.attr && E.trie_slot >= 0)
-                        group_rows = std::max<uint64_t>(group_rows, tries[E.trie_slot]->lv[E.nattrs - 1].n);
+                if (E.trie_slot < 0) continue;
+                const lh_trie *t = tries[E.trie_slot];
+                for (uint32_t l = 0; l < t->nlevels; ++l)
+                    if (E.attrs[t->key_order[l]] == G.attr) dom = std::min<uint64_t>(dom, t->lv[l].n);
             }
+            if (G.card > 0) dom = std::min<uint64_t>(dom, G.card);
+            group_space = std::min<uint64_t>(group_space * std::max<uint64_t>(1, dom == UINT64_MAX ? 1 : dom), 1ull << 40);
         } else {
             if (G.edge >= q->n_edges || q->edges[G.edge].trie_slot < 0) return lh_fail(ctx, LH_EINVAL, "group %u: bad edge", k);
             const lh_trie *t = tries[q->edges[G.edge].trie_slot];
@@ -702,7 +709,10 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
                 return lh_fail(ctx, LH_EINVAL, "group %u: needs an int32 annotation column", k);
             jq.g_edge[k] = G.edge;
             jq.g_col[k] = (const int32_t *)t->anno[G.anno];
-            group_rows = std::max<uint64_t>(group_rows, t->lv[t->nlevels - 1].n);
+            // distinct values of an annotation column: at most its card, at
+            // most the rows of its relation
+            const uint64_t dom = G.card > 0 ? std::min<uint64_t>(G.card, t->lv[t->nlevels - 1].n) : t->lv[t->nlevels - 1].n;
+            group_space = std::min<uint64_t>(group_space * std::max<uint64_t>(1, dom), 1ull << 40);
         }
     }
     // implementation (Section 5): dense arrays for small declared domains,
@@ -759,10 +769,12 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
         LH_CU(cudaMemsetAsync(r->d_gcount, 0, r->ngroups * sizeof(uint64_t), ctx->stream));
     }
     if (dr.mode_last == M_AGG && jq.gmode != G_DENSE) {
-        // the shared table: twice the larger of the feeding relations' rows
-        // (clamped to [2^12, 2^24]) unless the query gives a capacity
+        // the shared table: twice the bound on distinct key tuples (the
+        // product of the columns' domains: declared cards, else the distinct
+        // values their relations can hold), clamped to [2^12, 2^24] slots,
+        // unless the query gives a capacity
         uint64_t cap = q->group_capacity;
-        if (cap == 0) cap = std::min<uint64_t>(std::max<uint64_t>(2 * group_rows, 1ull << 12), 1ull << 24);
+        if (cap == 0) cap = std::min<uint64_t>(std::max<uint64_t>(2 * group_space, 1ull << 12), 1ull << 24);
         uint64_t c2 = 1;
         while (c2 < cap) c2 <<= 1;
         if (c2 > (1ull << 31)) return lh_fail(ctx, LH_EUNSUPPORTED, "group_capacity above 2^31");
@@ -889,6 +901,7 @@ extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v
     if (r->d_count) LH_CU(cudaMemcpy(&cnt, r->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
     if (r->d_elems) LH_CU(cudaMemcpy(&el, r->d_elems, sizeof(el), cudaMemcpyDeviceToHost));
     v->elements = el;
+    v->visited = r->visited;
     v->count = cnt + r->host_count;
     if (r->ngroups) {
         std::vector<double> gs(r->ngroups);
@@ -919,6 +932,74 @@ extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v
     v->c_col = r->c_col;
     v->c_val = r->c_val;
     return LH_OK;
+}
+
+namespace {
+// group totals -> (high, low) fp32 pair annotation columns
+__global__ void k_split_pair(const double *sum, const uint64_t *cnt, uint32_t use_count, uint64_t n, float *hi,
+                             float *lo) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const double v = use_count ? (double)cnt[i] : sum[i];
+        const float h = (float)v;
+        hi[i] = h;
+        lo[i] = (float)(v - (double)h);
+    }
+}
+}  // namespace
+
+extern "C" lh_status lh_join_to_trie(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan, lh_trie *const *tries,
+                                     uint32_t n_out, const uint32_t *out_attrs, const lh_layout_policy *layout,
+                                     lh_trie **out) {
+    if (!ctx || !q || !plan || !out || (n_out && !out_attrs)) return lh_fail(ctx, LH_EINVAL, "null argument");
+    *out = nullptr;
+    if (n_out == 0 || n_out > LH_MAX_GROUP || n_out > LH_MAX_LEVELS)
+        return lh_fail(ctx, LH_EINVAL, "1..%d output attributes", LH_MAX_LEVELS);
+    lh_query q2 = *q;
+    q2.n_group = n_out;
+    for (uint32_t k = 0; k < n_out; ++k) {
+        if (out_attrs[k] >= q->n_attrs) return lh_fail(ctx, LH_EINVAL, "output attribute out of range");
+        q2.group[k] = lh_group{0, -1, out_attrs[k], 0};
+    }
+    const bool counts = q->semiring == LH_COUNT_U64;
+    if (counts) q2.semiring = LH_SUM_F32_KAHAN;   // a tuple's weight: the number of join results under it
+    if (q2.group_impl == LH_GROUP_DENSE) q2.group_impl = LH_GROUP_AUTO;
+    if (q2.exec == LH_EXEC_AUTO) q2.exec = LH_EXEC_GENERIC;
+    lh_result *r = nullptr;
+    LH_TRY(lh_join_dispatch(ctx, &q2, plan, tries, &r, 0.0));
+    lh_result_view v;
+    lh_status s = lh_result_wait(ctx, r, &v);
+    float *hi = nullptr, *lo = nullptr;
+    const uint64_t G = v.ngroups;
+    if (s == LH_OK && !v.group_keys) s = lh_fail(ctx, LH_EUNSUPPORTED, "the join did not produce key tuples");
+    if (s == LH_OK) s = lh_alloc(ctx, &hi, std::max<uint64_t>(G, 1));
+    if (s == LH_OK) s = lh_alloc(ctx, &lo, std::max<uint64_t>(G, 1));
+    if (s == LH_OK && G) {
+        const unsigned g = lh_blocks(G, 256, (unsigned)ctx->num_sms * 8);
+        LH_TRACED(ctx, "k_split_pair", k_split_pair<<<g, 256, 0, ctx->stream>>>(v.group_sum, v.group_count, counts ? 1u : 0u,
+                                                                           G, hi, lo));
+    }
+    if (s == LH_OK) {
+        lh_relation_desc rel;
+        memset(&rel, 0, sizeof(rel));
+        rel.nrows = G;
+        rel.nkeys = n_out;
+        uint32_t order[LH_MAX_LEVELS];
+        for (uint32_t k = 0; k < n_out; ++k) {
+            rel.keys[k] = v.group_keys + (size_t)k * G;
+            order[k] = k;
+        }
+        rel.nannos = 2;
+        rel.annos[0] = hi;
+        rel.annos[1] = lo;
+        rel.anno_types[0] = rel.anno_types[1] = LH_T_F32;
+        s = lh_build_trie(ctx, &rel, order, layout, LH_MERGE_FIRST, out);
+    }
+    if (s == LH_OK) s = lh_sync(ctx);   // the temporaries below are read by the build
+    lh_free(ctx, hi);
+    lh_free(ctx, lo);
+    lh_result_free(ctx, r);
+    return s;
 }
 
 extern "C" lh_status lh_result_free(lh_ctx *ctx, lh_result *r) {

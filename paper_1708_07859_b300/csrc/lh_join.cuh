@@ -7,6 +7,7 @@ struct lh_result {
     uint64_t *d_count = nullptr;   // device counter (COUNT without GROUP BY)
     uint64_t host_count = 0;       // counts the driver resolved on the host
     uint64_t *d_elems = nullptr;   // intersection input elements examined
+    uint64_t visited = 0;          // elements the intersections read (candidates + one probe per other set)
     uint32_t ngroups = 0;
     double *d_gsum = nullptr;
     uint64_t *d_gcount = nullptr;

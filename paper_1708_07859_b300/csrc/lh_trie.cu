@@ -992,6 +992,94 @@ extern "C" lh_status lh_filter_trie(lh_ctx *ctx, const int32_t *col, uint64_t n,
     return LH_OK;
 }
 
+// ------------------------------------------------ selection pushed into a build
+
+namespace {
+__global__ void k_where_flags(lh_row_filter f0, lh_row_filter f1, lh_row_filter f2, lh_row_filter f3, uint32_t nf,
+                              uint64_t n, uint32_t *flag) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        bool ok = true;
+        const lh_row_filter fs[4] = {f0, f1, f2, f3};
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k)
+            if (k < nf) {
+                const int32_t v = fs[k].col[i];
+                ok = ok && v >= fs[k].lo && v <= fs[k].hi;
+            }
+        flag[i] = ok ? 1u : 0u;
+    }
+}
+
+template <class T>
+__global__ void k_where_gather(const T *src, const uint32_t *flag, const uint32_t *pos, uint64_t n, T *dst) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        if (flag[i]) dst[pos[i]] = src[i];
+}
+
+template <class T>
+lh_status where_gather(lh_ctx *ctx, const void *src, const uint32_t *flag, const uint32_t *pos, uint64_t n,
+                       uint64_t cnt, void **dst) {
+    T *d = nullptr;
+    LH_TRY(lh_alloc(ctx, &d, std::max<uint64_t>(cnt, 1)));
+    const unsigned G = (unsigned)std::min<uint64_t>(lh_blocks(n, 256), (uint64_t)ctx->num_sms * 16);
+    if (n) LH_TRACED(ctx, "k_where_gather", k_where_gather<T><<<G, 256, 0, ctx->stream>>>((const T *)src, flag, pos, n, d));
+    *dst = d;
+    return LH_OK;
+}
+}  // namespace
+
+extern "C" lh_status lh_build_trie_where(lh_ctx *ctx, const lh_relation_desc *rel, const uint32_t *key_order,
+                                         const lh_layout_policy *layout, lh_merge merge, const lh_row_filter *where,
+                                         uint32_t n_where, lh_trie **out) {
+    if (!ctx || !rel || !out) return lh_fail(ctx, LH_EINVAL, "null argument");
+    if (n_where > 4 || (n_where && !where)) return lh_fail(ctx, LH_EINVAL, "0..4 row filters");
+    for (uint32_t k = 0; k < n_where; ++k)
+        if (!where[k].col && rel->nrows) return lh_fail(ctx, LH_EINVAL, "row filter %u: null column", k);
+    if (rel->nkeys == 0 || rel->nkeys > LH_MAX_LEVELS || rel->nannos > LH_MAX_ANNOS)
+        return lh_fail(ctx, LH_EINVAL, "bad relation shape");
+    if (n_where == 0) return lh_build_trie(ctx, rel, key_order, layout, merge, out);
+    const uint64_t n = rel->nrows;
+    if (n >= (1ull << 32)) return lh_fail(ctx, LH_EOVERFLOW, "more than 2^32-1 rows");
+    lh_row_filter f[4] = {};
+    for (uint32_t k = 0; k < n_where; ++k) f[k] = where[k];
+    for (uint32_t k = n_where; k < 4; ++k) f[k] = f[0];
+    uint32_t *flag = nullptr, *pos = nullptr;
+    lh_status s = lh_alloc(ctx, &flag, std::max<uint64_t>(n, 1));
+    if (s == LH_OK) s = lh_alloc(ctx, &pos, n + 1);
+    const unsigned G = (unsigned)std::min<uint64_t>(lh_blocks(n, 256), (uint64_t)ctx->num_sms * 16);
+    if (s == LH_OK && n) LH_TRACED(ctx, "k_where_flags", k_where_flags<<<G, 256, 0, ctx->stream>>>(f[0], f[1], f[2], f[3], n_where, n, flag));
+    if (s == LH_OK) s = lh_scan_u32_to_u32(ctx, flag, pos, n);
+    uint32_t cnt = 0;
+    if (s == LH_OK) s = lh_readback(ctx, pos + n, sizeof(uint32_t), &cnt);
+    // the selected rows as a relation of their own, then the ordinary build
+    lh_relation_desc sel = *rel;
+    sel.nrows = cnt;
+    std::vector<void *> temps;
+    for (uint32_t c = 0; c < rel->nkeys && s == LH_OK; ++c) {
+        void *d = nullptr;
+        s = where_gather<uint32_t>(ctx, rel->keys[c], flag, pos, n, cnt, &d);
+        temps.push_back(d);
+        sel.keys[c] = (const uint32_t *)d;
+    }
+    for (uint32_t c = 0; c < rel->nannos && s == LH_OK; ++c) {
+        void *d = nullptr;
+        switch (rel->anno_types[c]) {
+            case LH_T_F64: s = where_gather<uint64_t>(ctx, rel->annos[c], flag, pos, n, cnt, &d); break;
+            case LH_T_I8: s = where_gather<uint8_t>(ctx, rel->annos[c], flag, pos, n, cnt, &d); break;
+            default: s = where_gather<uint32_t>(ctx, rel->annos[c], flag, pos, n, cnt, &d); break;
+        }
+        temps.push_back(d);
+        sel.annos[c] = d;
+    }
+    if (s == LH_OK) s = lh_build_trie(ctx, &sel, key_order, layout, merge, out);
+    lh_free(ctx, flag);
+    lh_free(ctx, pos);
+    for (void *p : temps) lh_free(ctx, p);
+    return s;
+}
+
 extern "C" lh_status lh_trie_free(lh_ctx *ctx, lh_trie *t) {
     if (!ctx || !t) return LH_EINVAL;
     lh_trie_release(ctx, t);

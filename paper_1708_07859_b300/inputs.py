@@ -277,6 +277,39 @@ def star_schema(n_fact: int = 60_000_000, dims=DIM_SIZES, seed: int = SEED_BASE 
     }
 
 
+BI_SIZES = {"fact": 60_000_000, "orders": 15_000_000, "customer": 1_500_000, "supplier": 100_000,
+            "nation": 25, "region": 5}
+
+
+def bi_schema(sizes=None, seed: int = SEED_BASE + 6):
+    """A six-relation BI schema shaped like the paper's two-node example
+    query (Section 3.1: a fact relation over (order, supplier), orders over
+    (order, customer), customer and supplier over a shared nation key, nation
+    over a region key, region): every relation's first key is its row id;
+    foreign keys uniform; fact price fp64 U[900, 105000] and discount
+    U{0..10} hundredths; orders carry a date U[0, 2557); region and nation a
+    name code (their row id).  Relation and column names are this
+    generator's own."""
+    z = dict(BI_SIZES)
+    z.update(sizes or {})
+    rng = _rng(seed)
+    u32 = lambda hi, n: rng.integers(0, hi, size=n, dtype=np.int64).astype(np.uint32)
+    nf = z["fact"]
+    return {
+        "sizes": z,
+        "fact_order": u32(z["orders"], nf), "fact_supp": u32(z["supplier"], nf),
+        "price": rng.uniform(900.0, 105000.0, size=nf),
+        "disc": rng.integers(0, 11, size=nf, dtype=np.int64).astype(np.int8),
+        "order_cust": u32(z["customer"], z["orders"]),
+        "order_date": rng.integers(0, DATE_DAYS, size=z["orders"], dtype=np.int64).astype(np.int32),
+        "cust_nation": u32(z["nation"], z["customer"]),
+        "supp_nation": u32(z["nation"], z["supplier"]),
+        "nation_region": u32(z["region"], z["nation"]),
+        "nation_name": np.arange(z["nation"], dtype=np.int32),
+        "region_name": np.arange(z["region"], dtype=np.int32),
+    }
+
+
 def date_range_for_selectivity(sel: float):
     """Inclusive [lo, hi] day range on d1_date keeping about ``sel`` of days."""
     width = max(1, int(round(sel * DATE_DAYS)))

@@ -52,6 +52,10 @@ class RelationDesc(C.Structure):
                 ("key_bound", C.c_uint32 * MAX_LEVELS)]
 
 
+class RowFilter(C.Structure):
+    _fields_ = [("col", C.c_void_p), ("lo", C.c_int32), ("hi", C.c_int32)]
+
+
 class LayoutPolicy(C.Structure):
     _fields_ = [("bs_ratio", C.c_uint32), ("bs_min_card", C.c_uint32)]
 
@@ -109,7 +113,7 @@ class ResultView(C.Structure):
                 ("nrows", C.c_uint64), ("y", C.c_void_p), ("nnz", C.c_uint64), ("c_row", C.c_void_p),
                 ("c_off", C.c_void_p), ("c_col", C.c_void_p), ("c_val", C.c_void_p),
                 ("elements", C.c_uint64), ("n_group_cols", C.c_uint32), ("group_keys", C.c_void_p),
-                ("group_impl", C.c_uint32)]
+                ("group_impl", C.c_uint32), ("visited", C.c_uint64)]
 
 
 class TraceEntry(C.Structure):
@@ -153,6 +157,10 @@ EXPORTS = {
     "lh_edge_key_order": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
     "lh_plan_explain": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_join_aggregate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_join_to_trie": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
+                        C.c_void_p],
+    "lh_build_trie_where": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_uint32,
+                            C.c_void_p],
     "lh_result_wait": [C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_result_free": [C.c_void_p, C.c_void_p],
     "lh_dense_matmul": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
@@ -276,10 +284,13 @@ class Context:
         self._check(lib().lh_set_stream(self.h, C.c_void_p(s.cuda_stream)))
 
     # --- tries -----------------------------------------------------------
-    def build_trie(self, keys, key_order=None, annos=(), merge=MERGE_SUM, layout=None, key_bounds=None):
+    def build_trie(self, keys, key_order=None, annos=(), merge=MERGE_SUM, layout=None, key_bounds=None,
+                   where=None):
         """keys: list of CUDA int32/uint32 tensors (same length); annos: list
         of (tensor, lh_dtype); key_bounds: optional domain size per key
-        column (every value below it).  Returns a Trie."""
+        column (every value below it); where: optional row selections
+        [(int32 tensor per row, lo, hi), ...] (lh_build_trie_where).
+        Returns a Trie."""
         desc = RelationDesc()
         for i, b in enumerate(key_bounds or ()):
             desc.key_bound[i] = int(b)
@@ -296,9 +307,27 @@ class Context:
         if layout is not None:
             pol = LayoutPolicy(*layout)
         out = C.c_void_p()
-        self._check(lib().lh_build_trie(self.h, C.byref(desc), order,
-                                        C.byref(pol) if pol is not None else None, merge, C.byref(out)))
-        return Trie(self, out, keep=(keys, annos))
+        if where:
+            filt = (RowFilter * len(where))(*[RowFilter(c.data_ptr(), int(lo), int(hi)) for c, lo, hi in where])
+            self._check(lib().lh_build_trie_where(self.h, C.byref(desc), order,
+                                                  C.byref(pol) if pol is not None else None, merge, filt,
+                                                  len(where), C.byref(out)))
+        else:
+            self._check(lib().lh_build_trie(self.h, C.byref(desc), order,
+                                            C.byref(pol) if pol is not None else None, merge, C.byref(out)))
+        return Trie(self, out, keep=(keys, annos, where))
+
+    def join_to_trie(self, q, plan, tries, out_attrs, layout=None):
+        """The join's result projected onto out_attrs, aggregated, as a Trie
+        (lh_join_to_trie): levels in out_attrs order, annotation columns 0/1
+        the fp32 (high, low) pair of each tuple's aggregate."""
+        arr = (C.c_void_p * max(1, len(tries)))(*[t.h.value for t in tries])
+        oa = (C.c_uint32 * len(out_attrs))(*out_attrs)
+        pol = LayoutPolicy(*layout) if layout is not None else None
+        out = C.c_void_p()
+        self._check(lib().lh_join_to_trie(self.h, C.byref(q), C.byref(plan), arr, len(out_attrs), oa,
+                                          C.byref(pol) if pol is not None else None, C.byref(out)))
+        return Trie(self, out)
 
     def filter_trie(self, col, lo, hi, layout=None):
         pol = LayoutPolicy(*layout) if layout is not None else None

@@ -45,8 +45,24 @@ def test_struct_sizes_match_header_layout(lhlib):
 
 def test_committed_dram_traffic_matches_the_kernel_source():
     """The DRAM traffic the bench reports for its dominant kernel comes from a
-    committed ncu capture keyed by a hash of the kernel's source; the capture
-    is current for the source as committed (the bench reports null otherwise)."""
+    committed ncu capture keyed by a hash of the kernel's source: the bench
+    reports the captured bytes (scaled by rows when the capture ran a smaller
+    case) while the source is unchanged, and null once it has changed."""
+    import hashlib
+    import json
     import bench
-    assert bench.dram_traffic("k_spgemm_esc", 1 << 19) == 1096105472
-    assert bench.dram_traffic("k_spgemm_esc", 1 << 20) == 2 * 1096105472
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+        recs = json.load(f)
+    assert recs
+    for name, rec in recs.items():
+        text = open(os.path.join(ROOT, "paper_1708_07859_b300", "csrc", rec["source"])).read()
+        a = text.find(rec["begin"])
+        b = text.find(rec["end"], a + 1)
+        current = a >= 0 and b >= 0 and hashlib.sha256(text[a:b].encode()).hexdigest() == rec["source_sha256"]
+        got = bench.dram_traffic(name, 2 * rec.get("rows", 1))
+        if current:
+            scale = 2 if rec.get("scales_with_rows") else 1
+            assert got == scale * rec["bytes_per_launch"]
+        else:
+            assert got is None
+        assert "--clock-control none" in rec["capture"]

@@ -331,6 +331,55 @@ def test_star_sum_keys_brute_force(orc):
         assert want[tuple(kk)][1] == int(cc) and math.isclose(want[tuple(kk)][0], ss, rel_tol=1e-12)
 
 
+def test_bi_q5_brute_force(orc):
+    """The six-relation BI join by nested loops over every tuple of every
+    relation, checking each join condition (the plain definition), on a tiny
+    instance."""
+    z = {"fact": 40, "orders": 7, "customer": 5, "supplier": 4, "nation": 3, "region": 2}
+    d = gen.bi_schema(z, seed=7)
+    region, dates = 1, (300, 2000)
+    gs, gc = orc.bi_q5(d, region, dates)
+    want = {}
+    for f in range(z["fact"]):
+        for o in range(z["orders"]):
+            if d["fact_order"][f] != o or not (dates[0] <= d["order_date"][o] <= dates[1]):
+                continue
+            for c in range(z["customer"]):
+                if d["order_cust"][o] != c:
+                    continue
+                for s_ in range(z["supplier"]):
+                    if d["fact_supp"][f] != s_:
+                        continue
+                    for n in range(z["nation"]):
+                        if d["cust_nation"][c] != n or d["supp_nation"][s_] != n:
+                            continue
+                        for r in range(z["region"]):
+                            if d["nation_region"][n] != r or d["region_name"][r] != region:
+                                continue
+                            g = int(d["nation_name"][n])
+                            a = want.setdefault(g, [0.0, 0])
+                            a[0] += float(d["price"][f]) * (1 - int(d["disc"][f]) / 100.0)
+                            a[1] += 1
+    assert {g: int(gc[g]) for g in np.flatnonzero(gc)} == {g: v[1] for g, v in want.items()}
+    for g, (s_, c) in want.items():
+        assert math.isclose(gs[g], s_, rel_tol=1e-12)
+
+
+def test_bi_q5_all_pass_total(orc):
+    """With every region and date admitted, the groups add up to the fact
+    rows whose customer and supplier share a nation."""
+    d = gen.bi_schema({"fact": 20000, "orders": 3000, "customer": 500, "supplier": 80, "nation": 7, "region": 3},
+                      seed=8)
+    tot_s, tot_c = 0.0, 0
+    for reg in range(3):
+        gs, gc = orc.bi_q5(d, reg, (0, 10 ** 6))
+        tot_s += gs.sum()
+        tot_c += int(gc.sum())
+    same = d["cust_nation"][d["order_cust"][d["fact_order"]]] == d["supp_nation"][d["fact_supp"]]
+    assert tot_c == int(same.sum())
+    assert math.isclose(tot_s, math.fsum(d["price"][same] * (1 - d["disc"][same] / 100.0)), rel_tol=1e-12)
+
+
 def test_filter_keys_plain(orc):
     col = np.array([5, 1, 9, 3, 7, 3], np.int32)
     assert orc.filter_keys(col, 3, 7).tolist() == [0, 3, 4, 5]
