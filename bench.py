@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--no-isect", action="store_true", help="skip the Figure 4a intersection batches")
     ap.add_argument("--isect-only", action="store_true", help="run only the Figure 4a intersection batches")
     ap.add_argument("--no-extras", action="store_true", help="skip the planner and batched-launch comparisons")
-    ap.add_argument("--extras-only", action="store_true", help="run only the planner and batched comparisons")
+    ap.add_argument("--extras-only", action="store_true", help="run only the WCOJ extras (no headline step)")
+    ap.add_argument("--only", default="", help="comma list of extras to run alone: triangle, star, batched, "
+                                               "planner, ghd, dense_mv, fig4a")
     return ap.parse_args()
 
 
@@ -588,7 +590,7 @@ def ghd_compare(ctx, lh, reps=3):
         same = sorted(res) == sorted(ref) and all(res[k][1] == ref[k][1] and
                                                   abs(res[k][0] - ref[k][0]) <= 1e-9 * abs(ref[k][0]) for k in res)
         out[name] = {"ms": statistics.median(ts), "nodes": len(plan.nodes()), "fhw": plan.fhw,
-                     "groups": len(res), "same_groups": bool(same)}
+                     "groups": len(res), "same_groups": bool(same), "node_log": plan.log}
     out["pushdown_speedup"] = out["ghd_in_node"]["ms"] / out["ghd_pushdown"]["ms"]
     out["vs_one_node"] = out["one_node"]["ms"] / out["ghd_pushdown"]["ms"]
     return out
@@ -724,6 +726,17 @@ def main():
         dist_init("nccl")
     dev_id = torch.cuda.current_device()
     from paper_1708_07859_b300 import lh
+    if args.only:
+        ctx = lh.Context()
+        l2 = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+        hbm = load_peaks()[0]
+        run = {"triangle": lambda: triangle_wcoj(ctx, lh), "star": lambda: star_join(ctx, lh, hbm),
+               "batched": lambda: batched_compare(ctx, lh, hbm, l2), "planner": lambda: planner_compare(ctx, lh),
+               "ghd": lambda: ghd_compare(ctx, lh), "dense_mv": lambda: dense_mv(ctx, lh, hbm, l2),
+               "fig4a": lambda: intersect_fig4a(ctx, lh, hbm, l2)}
+        print(json.dumps({k: run[k]() for k in args.only.split(",")}))
+        ctx.close()
+        return 0
     if args.isect_only or args.extras_only:
         ctx = lh.Context()
         l2 = torch.empty(64 << 20, dtype=torch.float32, device="cuda")

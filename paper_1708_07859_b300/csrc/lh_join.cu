@@ -168,8 +168,8 @@ __global__ void k_ht_scatter(HTab H, uint32_t ncol, const uint64_t *pos, uint64_
     }
 }
 
-__device__ __forceinline__ uint32_t find_entry(const uint64_t *off, uint32_t nF, uint64_t c) {
-    uint32_t lo = 0, hi = nF;  // off[lo] <= c < off[hi]
+__device__ __forceinline__ uint32_t find_entry(const uint64_t *off, uint32_t nF, uint64_t c, uint32_t lo = 0) {
+    uint32_t hi = nF;  // off[lo] <= c < off[hi]
     while (hi - lo > 1) {
         uint32_t mid = (lo + hi) >> 1;
         if (__ldg(off + mid) <= c) lo = mid;
@@ -177,6 +177,12 @@ __device__ __forceinline__ uint32_t find_entry(const uint64_t *off, uint32_t nF,
     }
     return lo;
 }
+
+// Frontier entries of one block-iteration of candidates: the block's first
+// and last candidates are located once in the global offsets, the offsets
+// in between are staged in shared memory, and every thread finds its entry
+// there (a few shared loads instead of a search over the whole frontier).
+constexpr uint32_t kWin = 256;
 
 __global__ void k_sizes(JQuery q, uint32_t d, const uint32_t *posF, uint32_t nF, uint32_t capF,
                         uint32_t *size, uint8_t *drv, unsigned long long *elems) {
@@ -257,6 +263,8 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
         }
         __syncthreads();
     }
+    __shared__ uint64_t s_win[kWin];
+    __shared__ uint32_t s_ent[2];
     uint32_t my_count = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t base = c0 + (uint64_t)blockIdx.x * blockDim.x; base < c1; base += stride) {
@@ -264,8 +272,30 @@ __global__ void __launch_bounds__(kThreads) k_expand(JQuery q, uint32_t d, const
         bool ok = c < c1;
         uint32_t i = 0, x = 0;
         uint32_t npos[LH_MAX_EDGES];
+        __syncthreads();   // the previous iteration is done with the window
+        if (threadIdx.x == 0) {
+            const uint32_t e0 = find_entry(off, nF, base);
+            s_ent[0] = e0;
+            s_ent[1] = find_entry(off, nF, min(base + blockDim.x, c1) - 1, e0);
+        }
+        __syncthreads();
+        const uint32_t e0 = s_ent[0], win = s_ent[1] - e0 + 1;
+        if (win <= kWin) {
+            for (uint32_t t = threadIdx.x; t < win; t += blockDim.x) s_win[t] = __ldg(off + e0 + t);
+            __syncthreads();
+        }
         if (ok) {
-            i = find_entry(off, nF, c);
+            if (win <= kWin) {
+                uint32_t lo = 0, hi = win;  // s_win[lo] <= c < s_win[hi] (hi = win: beyond the window)
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_win[mid] <= c) lo = mid;
+                    else hi = mid;
+                }
+                i = e0 + lo;
+            } else {
+                i = find_entry(off, e0 + win, c, e0);
+            }
             const uint32_t j = (uint32_t)(c - off[i]);
             const uint32_t p0 = drv[i];
             const JEdge &E0 = q.E[D.e[p0]];

@@ -558,104 +558,6 @@ __global__ void __launch_bounds__(kEscWarps * 32, 6) k_spgemm_esc(
     }
 }
 
-// ---- rows written straight into C ---------------------------------------------
-// When every row takes the sort-based path, one persistent kernel writes C
-// directly: a block claims a tile of kFzRows consecutive rows by ticket (one
-// row per warp), computes them into shared memory, and finds the tile's
-// offset in C by decoupled look-back over the tiles before it (a tile
-// publishes its own entry count as soon as it has it, then its inclusive
-// prefix once known); the rows' results are then copied out with coalesced
-// stores and their CSR offsets written.  No staging array in global memory
-// and no compaction pass.  The grid never exceeds the resident blocks, so a
-// tile's predecessors are all running; every wait is bounded.
-constexpr int kFzRows = kEscWarps;                  // rows per tile, one per warp
-constexpr unsigned long long kFzAgg = 1ull << 62;   // tile state: own count published
-constexpr unsigned long long kFzInc = 2ull << 62;   // tile state: inclusive prefix published
-constexpr unsigned long long kFzVal = (1ull << 62) - 1;
-constexpr uint32_t kFzSpin = 1u << 24;
-
-struct FzSmem {
-    EscSmem esc[kEscWarps];
-    uint32_t ocol[kEscWarps][kEscPairs];
-    float oval[kEscWarps][kEscPairs];
-    uint32_t rcnt[kFzRows];
-    uint32_t roff[kFzRows];
-    unsigned long long excl;
-    uint32_t tile;
-    uint32_t ok;
-};
-
-template <class K>
-__global__ void __launch_bounds__(kEscWarps * 32, 5) k_spgemm_fused(
-    DTrie A, const float *av, DTrie B, const float *bv, uint32_t nA0, uint32_t ntiles,
-    unsigned long long *state, uint32_t *ticket, uint64_t *c_off, uint32_t *c_col, float *c_val,
-    uint32_t *status) {
-    extern __shared__ __align__(16) unsigned char fz_raw[];
-    FzSmem &F = *(FzSmem *)fz_raw;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    while (true) {
-        if (threadIdx.x == 0) F.tile = atomicAdd(ticket, 1u);
-        __syncthreads();
-        const uint32_t tile = F.tile;
-        if (tile >= ntiles) break;
-        const uint32_t p = tile * kFzRows + warp;
-        uint32_t n = 0;
-        if (p < nA0) n = esc_row<K>(A, av, B, bv, p, F.esc[warp], lane, F.ocol[warp], F.oval[warp]);
-        if (lane == 0) F.rcnt[warp] = n;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t v = lane < kFzRows ? F.rcnt[lane] : 0u;
-            uint32_t incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(LH_FULL, incl, o);
-                if (lane >= o) incl += t;
-            }
-            if (lane < kFzRows) F.roff[lane] = incl - v;
-            const unsigned long long agg = __shfl_sync(LH_FULL, incl, 31);
-            if (lane == 0) {
-                unsigned long long excl = 0;
-                bool ok = true;
-                if (tile == 0) {
-                    atomicExch(state, kFzInc | agg);
-                } else {
-                    atomicExch(state + tile, kFzAgg | agg);
-                    uint32_t spins = 0;
-                    for (uint32_t j = tile - 1;;) {
-                        const unsigned long long st = *(volatile unsigned long long *)(state + j);
-                        if ((st & ~kFzVal) == 0) {
-                            if (++spins > kFzSpin) {
-                                ok = false;
-                                break;
-                            }
-                            __nanosleep(32);
-                            continue;
-                        }
-                        excl += st & kFzVal;
-                        if (st & kFzInc) break;
-                        --j;
-                    }
-                    if (ok) atomicExch(state + tile, kFzInc | (excl + agg));
-                }
-                if (!ok) lh_set_status(status, LH_ETIMEOUT);
-                F.excl = excl;
-                F.ok = ok ? 1u : 0u;
-                if (ok && tile == ntiles - 1) c_off[nA0] = excl + agg;
-            }
-        }
-        __syncthreads();
-        if (F.ok && p < nA0) {
-            const uint64_t base = F.excl + F.roff[warp];
-            if (lane == 0) c_off[p] = base;
-            for (uint32_t i = lane; i < n; i += 32) {
-                c_col[base + i] = F.ocol[warp][i];
-                c_val[base + i] = F.oval[warp][i];
-            }
-        }
-        __syncthreads();   // the tile's buffers and F.tile are reused
-    }
-}
-
 __global__ void k_spgemm_gather(uint32_t nA0, const uint64_t *tmp_off, const uint64_t *c_off,
                                 const uint32_t *tcol, const float *tval, uint32_t *ccol, float *cval) {
     const int lane = threadIdx.x & 31;
@@ -745,46 +647,6 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         STEP(lh_readback(ctx, n_hash, sizeof(h), h));
         U = h[0];
         hash_rows = h[1];
-    }
-    if (s == LH_OK && n0 && !hash_rows) {
-        // every row takes the sort-based path: write C directly (no staging)
-        const uint32_t ntiles = (n0 + kFzRows - 1) / kFzRows;
-        unsigned long long *state = nullptr;
-        uint32_t *ticket = nullptr;
-        STEP(res_alloc(ctx, r, &r->c_col, std::max<uint64_t>(U, 1)));
-        STEP(res_alloc(ctx, r, &r->c_val, std::max<uint64_t>(U, 1)));
-        STEP(lh_alloc(ctx, &state, (size_t)ntiles + 1));
-        if (s == LH_OK) {
-            ticket = (uint32_t *)(state + ntiles);
-            cudaMemsetAsync(state, 0, ((size_t)ntiles + 1) * sizeof(unsigned long long), ctx->stream);
-            const bool narrow = b->key_bits[1] <= 24;
-            const size_t smem = sizeof(FzSmem);
-            int per_sm = 0;
-            if (narrow) {
-                cudaFuncSetAttribute(k_spgemm_fused<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spgemm_fused<uint32_t>, kEscWarps * 32, smem);
-            } else {
-                cudaFuncSetAttribute(k_spgemm_fused<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spgemm_fused<uint64_t>, kEscWarps * 32, smem);
-            }
-            // a persistent grid no larger than what is resident at once
-            const unsigned g = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * std::max(1, per_sm));
-            if (narrow)
-                LH_TRACED(ctx, "k_spgemm_fused", k_spgemm_fused<uint32_t><<<g, kEscWarps * 32, smem, ctx->stream>>>(
-                    A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ntiles, state, ticket, r->c_off,
-                    r->c_col, r->c_val, ctx->d_status));
-            else
-                LH_TRACED(ctx, "k_spgemm_fused", k_spgemm_fused<uint64_t><<<g, kEscWarps * 32, smem, ctx->stream>>>(
-                    A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ntiles, state, ticket, r->c_off,
-                    r->c_col, r->c_val, ctx->d_status));
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "spgemm: %s", cudaGetErrorString(e));
-        }
-        lh_free(ctx, state);
-        if (s == LH_OK) r->nnz_pending = true;
-        lh_free(ctx, ub); lh_free(ctx, cnt); lh_free(ctx, tmp_off); lh_free(ctx, gcap); lh_free(ctx, goff);
-        lh_free(ctx, n_hash);
-        return s;
     }
     if (s == LH_OK && hash_rows) {
         // global hash tables only for rows whose products overflow shared memory

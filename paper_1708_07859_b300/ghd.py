@@ -367,6 +367,8 @@ class Executor:
         return specs
 
     def _eval(self, node, out_vertices, group, pushdown, owned):
+        import time
+        t_start = time.perf_counter()
         lh = self.lh
         specs = self._specs(node, pushdown)
         verts = sorted(set(v for s in specs for v in s[2]))
@@ -406,6 +408,7 @@ class Executor:
                                         merge=r.merge, where=where)
             owned.append(t)
             tries.append(t)
+        t_join = time.perf_counter()
         if is_root:
             r = self.ctx.join_aggregate(q, plan, tries)
             try:
@@ -413,10 +416,17 @@ class Executor:
                 gs, gc = r.groups()
             finally:
                 r.free()
-            return gs, gc, v
-        t = self.ctx.join_to_trie(q, plan, tries, [loc[v] for v in out_vertices])
-        owned.append(t)
-        return t
+            out = (gs, gc, v)
+        else:
+            out = self.ctx.join_to_trie(q, plan, tries, [loc[v] for v in out_vertices])
+            owned.append(out)
+        t_end = time.perf_counter()
+        # per node: its plan order, the time of its own join, and the
+        # wall time including its children and trie builds
+        self.log.append({"bag": sorted(node.bag), "relations": [self.hg.edges[i].name for i in node.edges],
+                         "order": [verts[a] for a in plan.order_list()], "join_ms": (t_end - t_join) * 1e3,
+                         "incl_ms": (t_end - t_start) * 1e3})
+        return out
 
     def run(self, ghd: GHD, group, pushdown=True):
         """Executes the plan; group: [(vertex, card)] GROUP BY key vertices
@@ -429,6 +439,7 @@ class Executor:
                 if e.selected and not self.rel[i].key_filters:
                     raise ValueError(f"relation {e.name}: a selection kept in its node needs key_filters")
         owned = []
+        self.log = []
         try:
             return self._eval(ghd.root, None, list(group), pushdown, owned)
         finally:

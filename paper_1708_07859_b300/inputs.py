@@ -295,9 +295,22 @@ def bi_schema(sizes=None, seed: int = SEED_BASE + 6):
     rng = _rng(seed)
     u32 = lambda hi, n: rng.integers(0, hi, size=n, dtype=np.int64).astype(np.uint32)
     nf = z["fact"]
+    # distinct (order, supplier) pairs, first occurrences in draw order: a
+    # fact row is identified by its key tuple
+    no, ns = z["orders"], z["supplier"]
+    if nf > no * ns:
+        raise ValueError("more fact rows than (order, supplier) pairs")
+    keys = np.zeros(0, dtype=np.uint64)
+    while keys.size < nf:
+        draw = rng.integers(0, no, size=nf + 64, dtype=np.int64).astype(np.uint64) * np.uint64(ns) + \
+            rng.integers(0, ns, size=nf + 64, dtype=np.int64).astype(np.uint64)
+        allk = np.concatenate([keys, draw])
+        _, first = np.unique(allk, return_index=True)
+        first.sort()
+        keys = allk[first][:nf]
     return {
         "sizes": z,
-        "fact_order": u32(z["orders"], nf), "fact_supp": u32(z["supplier"], nf),
+        "fact_order": (keys // np.uint64(ns)).astype(np.uint32), "fact_supp": (keys % np.uint64(ns)).astype(np.uint32),
         "price": rng.uniform(900.0, 105000.0, size=nf),
         "disc": rng.integers(0, 11, size=nf, dtype=np.int64).astype(np.int8),
         "order_cust": u32(z["customer"], z["orders"]),

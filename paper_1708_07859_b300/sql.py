@@ -402,6 +402,7 @@ def plan_and_run(ctx, text, catalog, pushdown=True, single_node=False):
     semiring = lh.SUM_F32_KAHAN
     ex = ghd.Executor(ctx, lh, hg, rels, semiring)
     gs, gc, view = ex.run(plan, list(zip(group_vertices, cards)), pushdown=pushdown)
+    plan.log = ex.log
     # dense groups over the key vertices -> requested group keys
     out = {}
     idx = np.flatnonzero(gc)

@@ -335,7 +335,7 @@ def test_bi_q5_brute_force(orc):
     """The six-relation BI join by nested loops over every tuple of every
     relation, checking each join condition (the plain definition), on a tiny
     instance."""
-    z = {"fact": 40, "orders": 7, "customer": 5, "supplier": 4, "nation": 3, "region": 2}
+    z = {"fact": 24, "orders": 7, "customer": 5, "supplier": 4, "nation": 3, "region": 2}
     d = gen.bi_schema(z, seed=7)
     region, dates = 1, (300, 2000)
     gs, gc = orc.bi_q5(d, region, dates)
