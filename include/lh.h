@@ -35,7 +35,7 @@ extern "C" {
 #define LH_MAX_ATTRS 6   /* key attributes of one query (hypergraph vertices) */
 #define LH_MAX_EDGES 8   /* relations of one query (hyperedges) */
 #define LH_MAX_ANNOS 4   /* annotation columns of one relation */
-#define LH_NFEAT 60      /* learned-planner feature vector length */
+#define LH_NFEAT 64      /* learned-planner feature vector length */
 #define LH_MAX_GROUP 6   /* GROUP BY columns of one query */
 
 typedef enum {
@@ -154,13 +154,17 @@ typedef enum { LH_MERGE_SUM = 0, LH_MERGE_FIRST = 1, LH_MERGE_PRICE_DISCOUNT = 2
 
 /* Per-set layout choice (Section 2.2: dense sets as bitsets, sparse sets as
  * sorted uint32).  A set of cardinality c spanning s = max - min + 1 values
- * gets a bitset when bs_ratio > 0, c >= bs_min_card and c * bs_ratio >= s.
- * NULL selects {32, 32}.  Every set keeps its sorted uint32 array (used to
- * iterate); a bitset set additionally has 32-bit words (base = min rounded
- * down to 128, word count a multiple of 4) and a per-word rank. */
+ * gets a bitset when its level's ratio r > 0, c >= bs_min_card and c * r >=
+ * s.  r is bs_ratio for every level, or level_ratio[l] for level l when
+ * per_level != 0 (a policy per trie level).  NULL selects {32, 32}.  Every
+ * set keeps its sorted uint32 array (used to iterate); a bitset set
+ * additionally has 32-bit words (base = min rounded down to 128, word count
+ * a multiple of 4) and a per-word rank. */
 typedef struct {
     uint32_t bs_ratio;
     uint32_t bs_min_card;
+    uint32_t per_level;
+    uint32_t level_ratio[LH_MAX_LEVELS];
 } lh_layout_policy;
 
 /* Build the trie of `rel` with level l holding key column key_order[l]
@@ -376,16 +380,20 @@ typedef struct {
     float predicted_log_ms;       /* learned model output (NaN if not used) */
     float measured_ms;            /* exhaustive timing of the chosen plan (NaN if not used) */
     uint32_t n_candidates;        /* plans considered */
+    uint32_t bs_ratio_inner;      /* layout ratio of trie levels >= 1 (bs_ratio: level 0) */
 } lh_plan_t;
 
 /* Planner options.  time_budget_ms bounds each exhaustive candidate run
  * (host-side: chunks stop being issued once it is exceeded; the candidate is
- * then ranked last).  policies: layout ratios tried (0 = uint only). */
+ * then ranked last).  policies: layout ratios tried (0 = uint only); with
+ * per_level != 0 every (level-0 ratio, inner-level ratio) pair of them is a
+ * candidate layout, else one ratio serves every level. */
 typedef struct {
     uint32_t n_policies;
     uint32_t policies[4];
     float time_budget_ms;
     uint32_t repeats;
+    uint32_t per_level;
 } lh_plan_opts;
 
 /* Choose an attribute order (and layout policy) for `q`.
@@ -590,8 +598,8 @@ lh_status lh_plan_time(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan, lh
  * levels: [0, 6) log2(1 + |relation|) per edge; [6, 31) per order position
  * d < 5: log2 set-size median, 90th percentile, maximum, level density, and
  * log2(1 + icost(v_d) x weight(v_d)) of the Section 4 cost model; [31, 56)
- * position x attribute one-hot; [56, 60) layout policy one-hot (ratio 0, 8,
- * 32, other). */
+ * position x attribute one-hot; [56, 60) one-hot of the level-0 layout
+ * ratio and [60, 64) of the inner levels' ratio (0, 8, 32, other). */
 lh_status lh_plan_features(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
                            lh_trie *const *tries, float *feat);
 

@@ -148,6 +148,7 @@ struct lh_trie {
     void *anno[LH_MAX_ANNOS] = {nullptr};
     uint32_t anno_type[LH_MAX_ANNOS] = {0};
     uint32_t bs_ratio = 0, bs_min_card = 0;
+    uint32_t level_ratio[LH_MAX_LEVELS] = {0};   // layout ratio of each level (0 = uint only)
     uint64_t bytes = 0;
     std::vector<void *> allocs;
 };

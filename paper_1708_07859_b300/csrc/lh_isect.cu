@@ -480,35 +480,16 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
             if (s < e) {
                 uint32_t ii = sw_split(pa, la, pb, lb, s);
                 uint32_t jj = s - ii;
-                // The thread's e - s merge outputs are the smallest of
-                // A[ii:] and B[jj:]: load 16 of each (past the slices'
-                // ends: 0xFFFFFFFF, above every value of a merge pair),
-                // merge them with a bitonic network in registers (B
-                // reversed, five half-cleaning steps: independent min/max
-                // pairs, no dependent shared loads), and count the outputs
-                // followed by an equal value -- with ties ordered A first,
-                // that is an A element whose B counterpart is the next
-                // output, each common value counted once.
-                uint32_t m[2 * kItems];
+                uint32_t a = pa[swz(ii)], b = pb[swz(jj)];
 #pragma unroll
                 for (int k = 0; k < kItems; ++k) {
-                    m[k] = (ii + k < la) ? pa[swz(ii + k)] : 0xFFFFFFFFu;
-                    m[2 * kItems - 1 - k] = (jj + k < lbx) ? pb[swz(jj + k)] : 0xFFFFFFFFu;
-                }
-#pragma unroll
-                for (int j = kItems; j > 0; j >>= 1) {
-#pragma unroll
-                    for (int t = 0; t < 2 * kItems; ++t) {
-                        if ((t & j) == 0) {
-                            const uint32_t lo = min(m[t], m[t + j]), hi = max(m[t], m[t + j]);
-                            m[t] = lo;
-                            m[t + j] = hi;
-                        }
+                    if (s + k < e) {
+                        const bool ta = a <= b;
+                        cnt += (a == b) ? 1u : 0u;  // a consumed while the B head equals it
+                        if (ta) a = pa[swz(++ii)];
+                        else b = pb[swz(++jj)];
                     }
                 }
-                const uint32_t n_out = e - s;
-#pragma unroll
-                for (int k = 0; k < kItems; ++k) cnt += ((uint32_t)k < n_out && m[k] == m[k + 1]) ? 1u : 0u;
             }
         } else if (kind == K_UBS || kind == K_PROBE) {
             uint32_t x[kItems];

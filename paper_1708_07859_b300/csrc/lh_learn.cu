@@ -275,7 +275,7 @@ int policy_index(uint32_t ratio) {
     }
 }
 
-lh_status features(lh_ctx *ctx, const lh_query *q, const uint32_t *order, uint32_t bs_ratio,
+lh_status features(lh_ctx *ctx, const lh_query *q, const uint32_t *order, uint32_t ratio0, uint32_t ratio_inner,
                    const lh_trie *const *edge_tries, float *f) {
     for (int i = 0; i < LH_NFEAT; ++i) f[i] = 0.f;
     uint64_t cards[LH_MAX_EDGES];
@@ -319,7 +319,8 @@ lh_status features(lh_ctx *ctx, const lh_query *q, const uint32_t *order, uint32
         f[6 + 5 * d + 4] = (float)std::log2(1.0 + (double)lh_icost_vertex(q, order, d) * (double)w[v]);
         if (v < 5) f[31 + 5 * d + v] = 1.f;
     }
-    f[56 + policy_index(bs_ratio)] = 1.f;
+    f[56 + policy_index(ratio0)] = 1.f;
+    f[60 + policy_index(ratio_inner)] = 1.f;
     return LH_OK;
 }
 
@@ -336,13 +337,41 @@ lh_merge merge_for(const lh_relation_desc *rel) {
     return LH_MERGE_SUM;
 }
 
+// a candidate layout: ratio of level 0 and of the deeper levels
+struct Pol {
+    uint32_t r0, r1;
+};
+
+lh_layout_policy policy_of(Pol p) {
+    lh_layout_policy pol{};
+    pol.bs_ratio = p.r0;
+    pol.bs_min_card = (p.r0 || p.r1) ? 32u : 0u;
+    pol.per_level = 1;
+    pol.level_ratio[0] = p.r0;
+    for (int l = 1; l < LH_MAX_LEVELS; ++l) pol.level_ratio[l] = p.r1;
+    return pol;
+}
+
+std::vector<Pol> candidate_policies(const lh_plan_opts *o) {
+    std::vector<Pol> out;
+    for (uint32_t i = 0; i < o->n_policies; ++i) {
+        if (!o->per_level) {
+            out.push_back({o->policies[i], o->policies[i]});
+            continue;
+        }
+        for (uint32_t j = 0; j < o->n_policies; ++j) out.push_back({o->policies[i], o->policies[j]});
+    }
+    return out;
+}
+
 struct TrieKey {
     const lh_relation_desc *rel;
     uint32_t order[LH_MAX_LEVELS];
-    uint32_t ratio;
+    uint32_t r0, r1;
     bool operator<(const TrieKey &o) const {
         if (rel != o.rel) return rel < o.rel;
-        if (ratio != o.ratio) return ratio < o.ratio;
+        if (r0 != o.r0) return r0 < o.r0;
+        if (r1 != o.r1) return r1 < o.r1;
         return memcmp(order, o.order, sizeof(order)) < 0;
     }
 };
@@ -353,18 +382,19 @@ struct TrieCache {
     ~TrieCache() {
         for (auto &kv : tries) lh_trie_free(ctx, kv.second);
     }
-    lh_status get(const lh_relation_desc *rel, const uint32_t *ko, uint32_t nk, uint32_t ratio, lh_trie **out) {
+    lh_status get(const lh_relation_desc *rel, const uint32_t *ko, uint32_t nk, Pol p, lh_trie **out) {
         TrieKey k;
         memset(&k, 0, sizeof(k));
         k.rel = rel;
-        k.ratio = ratio;
+        k.r0 = p.r0;
+        k.r1 = p.r1;
         for (uint32_t i = 0; i < nk; ++i) k.order[i] = ko[i];
         auto it = tries.find(k);
         if (it != tries.end()) {
             *out = it->second;
             return LH_OK;
         }
-        lh_layout_policy pol{ratio, ratio ? 32u : 0u};
+        const lh_layout_policy pol = policy_of(p);
         lh_trie *t = nullptr;
         LH_TRY(lh_build_trie(ctx, rel, ko, &pol, merge_for(rel), &t));
         tries[k] = t;
@@ -375,14 +405,14 @@ struct TrieCache {
 
 // tries of every edge of q under `order` (flat edges: null)
 lh_status edge_tries_for(TrieCache &cache, const lh_query *q, const lh_relation_desc *const *rels,
-                         const uint32_t *order, uint32_t ratio, lh_trie **tries) {
+                         const uint32_t *order, Pol pol, lh_trie **tries) {
     for (uint32_t e = 0; e < q->n_edges; ++e) {
         tries[e] = nullptr;
         if (q->edges[e].trie_slot < 0) continue;
         if (!rels[e]) return lh_fail(cache.ctx, LH_EINVAL, "edge %u: no relation", e);
         uint32_t ko[LH_MAX_LEVELS];
         if (!lh_key_order_for(q, order, q->n_attrs, e, ko)) return lh_fail(cache.ctx, LH_EINVAL, "edge %u: key order", e);
-        LH_TRY(cache.get(rels[e], ko, q->edges[e].nattrs, ratio, &tries[e]));
+        LH_TRY(cache.get(rels[e], ko, q->edges[e].nattrs, pol, &tries[e]));
     }
     return LH_OK;
 }
@@ -410,15 +440,16 @@ lh_status lh_plan_learned(lh_ctx *ctx, const lh_query *q, const lh_model *model,
     lh_candidate_orders(q, orders);
     TrieCache cache{ctx, {}};
     std::vector<float> feats;
-    std::vector<std::pair<size_t, uint32_t>> cand;
+    const std::vector<Pol> pols = candidate_policies(o);
+    std::vector<std::pair<size_t, Pol>> cand;
     for (size_t i = 0; i < orders.size(); ++i) {
         lh_trie *tr[LH_MAX_EDGES];
-        LH_TRY(edge_tries_for(cache, q, rels, orders[i].data(), 0, tr));
-        for (uint32_t pi = 0; pi < o->n_policies; ++pi) {
+        LH_TRY(edge_tries_for(cache, q, rels, orders[i].data(), Pol{0, 0}, tr));
+        for (const Pol &pl : pols) {
             float f[LH_NFEAT];
-            LH_TRY(features(ctx, q, orders[i].data(), o->policies[pi], tr, f));
+            LH_TRY(features(ctx, q, orders[i].data(), pl.r0, pl.r1, tr, f));
             feats.insert(feats.end(), f, f + LH_NFEAT);
-            cand.push_back({i, o->policies[pi]});
+            cand.push_back({i, pl});
         }
     }
     const uint32_t nc = (uint32_t)cand.size();
@@ -444,7 +475,8 @@ lh_status lh_plan_learned(lh_ctx *ctx, const lh_query *q, const lh_model *model,
     lh_weights(q, cards, w);
     const auto &bo = orders[cand[best].first];
     for (uint32_t i = 0; i < q->n_attrs; ++i) out->order[i] = bo[i];
-    out->bs_ratio = cand[best].second;
+    out->bs_ratio = cand[best].second.r0;
+    out->bs_ratio_inner = cand[best].second.r1;
     out->exec = lh_exec_for(q, out->order);
     out->cost = lh_cost_of(q, out->order, w);
     out->predicted_log_ms = pred[best];
@@ -463,17 +495,20 @@ lh_status lh_plan_exhaustive(lh_ctx *ctx, const lh_query *q, const lh_relation_d
     LH_CU(cudaEventCreate(&e1));
     double best_ms = 1e300;
     size_t best_i = 0;
-    uint32_t best_pol = 0, n = 0;
+    Pol best_pol{0, 0};
+    uint32_t n = 0;
     lh_status s = LH_OK;
     const double budget = o->time_budget_ms > 0 ? o->time_budget_ms : 0.0;
+    const std::vector<Pol> pols = candidate_policies(o);
     for (size_t i = 0; i < orders.size() && s == LH_OK; ++i) {
-        for (uint32_t pi = 0; pi < o->n_policies && s == LH_OK; ++pi) {
+        for (size_t pi = 0; pi < pols.size() && s == LH_OK; ++pi) {
             lh_trie *tr[LH_MAX_EDGES];
-            s = edge_tries_for(cache, q, rels, orders[i].data(), o->policies[pi], tr);
+            s = edge_tries_for(cache, q, rels, orders[i].data(), pols[pi], tr);
             if (s != LH_OK) break;
             lh_plan_t p = *out;
             for (uint32_t k = 0; k < q->n_attrs; ++k) p.order[k] = orders[i][k];
-            p.bs_ratio = o->policies[pi];
+            p.bs_ratio = pols[pi].r0;
+            p.bs_ratio_inner = pols[pi].r1;
             p.exec = LH_EXEC_AUTO;
             double tot = 0;
             bool timed_out = false;
@@ -500,7 +535,7 @@ lh_status lh_plan_exhaustive(lh_ctx *ctx, const lh_query *q, const lh_relation_d
             if (ms < best_ms) {
                 best_ms = ms;
                 best_i = i;
-                best_pol = o->policies[pi];
+                best_pol = pols[pi];
             }
         }
     }
@@ -509,7 +544,8 @@ lh_status lh_plan_exhaustive(lh_ctx *ctx, const lh_query *q, const lh_relation_d
     cudaEventDestroy(e1);
     LH_TRY(s);
     for (uint32_t k = 0; k < q->n_attrs; ++k) out->order[k] = orders[best_i][k];
-    out->bs_ratio = best_pol;
+    out->bs_ratio = best_pol.r0;
+    out->bs_ratio_inner = best_pol.r1;
     out->exec = lh_exec_for(q, out->order);
     out->measured_ms = (float)best_ms;
     out->n_candidates = n;
@@ -627,7 +663,7 @@ extern "C" lh_status lh_plan_features(lh_ctx *ctx, const lh_query *q, const lh_p
     if (!ctx || !q || !plan || !feat || !tries) return lh_fail(ctx, LH_EINVAL, "null argument");
     lh_trie *et[LH_MAX_EDGES];
     for (uint32_t e = 0; e < q->n_edges; ++e) et[e] = q->edges[e].trie_slot >= 0 ? tries[q->edges[e].trie_slot] : nullptr;
-    return features(ctx, q, plan->order, plan->bs_ratio, et, feat);
+    return features(ctx, q, plan->order, plan->bs_ratio, plan->bs_ratio_inner, et, feat);
 }
 
 extern "C" lh_status lh_plan_time(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan, lh_trie *const *tries,

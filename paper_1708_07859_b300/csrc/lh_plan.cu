@@ -145,6 +145,7 @@ lh_status lh_plan_cost(lh_ctx *ctx, const lh_query *q, const uint64_t *cards, lh
     for (uint32_t i = 0; i < q->n_attrs; ++i) out->order[i] = bo[i];
     out->cost = best;
     out->bs_ratio = 32;
+    out->bs_ratio_inner = 32;
     out->exec = lh_exec_for(q, out->order);
     out->predicted_log_ms = NAN;
     out->measured_ms = NAN;
@@ -204,7 +205,7 @@ extern "C" lh_status lh_plan(lh_ctx *ctx, const lh_query *q, lh_planner_kind kin
     LH_TRY(lh_plan_cost(ctx, q, cards, out));
     if (kind == LH_PLANNER_COST) return LH_OK;
     if (!rels) return lh_fail(ctx, LH_EINVAL, "learned and exhaustive planners need the relations");
-    lh_plan_opts o = opts ? *opts : lh_plan_opts{4, {0, 8, 32, 128}, 0.f, 1};
+    lh_plan_opts o = opts ? *opts : lh_plan_opts{4, {0, 8, 32, 128}, 0.f, 1, 0};
     if (o.n_policies == 0 || o.n_policies > 4) return lh_fail(ctx, LH_EINVAL, "1..4 layout policies");
     if (kind == LH_PLANNER_LEARNED) {
         if (!model) return lh_fail(ctx, LH_EINVAL, "learned planner needs a model");

@@ -558,7 +558,7 @@ static lh_status trie_layout(lh_ctx *ctx, lh_trie *t, LayoutPre *pre) {
         TrieLevel &L = t->lv[l];
         L.nsets = (l == 0) ? 1 : t->lv[l - 1].n;
         L.n_bs = 0;
-        any = any || (t->bs_ratio != 0 && L.n != 0);
+        any = any || (t->level_ratio[l] != 0 && L.n != 0);
     }
     if (pre) {
         for (uint32_t l = 0; l < t->nlevels; ++l) {
@@ -579,12 +579,12 @@ static lh_status trie_layout(lh_ctx *ctx, lh_trie *t, LayoutPre *pre) {
     }
     for (uint32_t l = 0; l < t->nlevels && s == LH_OK && any; ++l) {
         TrieLevel &L = t->lv[l];
-        if (t->bs_ratio == 0 || L.n == 0) continue;
+        if (t->level_ratio[l] == 0 || L.n == 0) continue;
         const uint32_t *poffs = (l == 0) ? nullptr : t->lv[l - 1].offs;
         if ((s = lh_alloc(ctx, &tmp_isbs[l], L.nsets)) != LH_OK) break;
         if ((s = lh_alloc(ctx, &tmp_words[l], L.nsets)) != LH_OK) break;
         LH_TRACED(ctx, "k_layout_decide", k_layout_decide<<<lh_blocks(L.nsets, T, 1 << 16), T, 0, ctx->stream>>>(
-            L.vals, poffs, L.nsets, (uint32_t)L.n, nullptr, nullptr, t->bs_ratio, t->bs_min_card, tmp_isbs[l],
+            L.vals, poffs, L.nsets, (uint32_t)L.n, nullptr, nullptr, t->level_ratio[l], t->bs_min_card, tmp_isbs[l],
             tmp_words[l], d_tot + 2 * l));
     }
     if (s == LH_OK && any) s = lh_readback(ctx, d_tot, sizeof(h_tot), h_tot);
@@ -696,6 +696,11 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
     t->nrows_in = rel->nrows;
     t->bs_ratio = pol.bs_ratio;
     t->bs_min_card = pol.bs_min_card;
+    bool any_ratio = false;
+    for (uint32_t l = 0; l < LH_MAX_LEVELS; ++l) {
+        t->level_ratio[l] = pol.per_level ? pol.level_ratio[l] : pol.bs_ratio;
+        any_ratio = any_ratio || (l < L && t->level_ratio[l] != 0);
+    }
     for (uint32_t l = 0; l < L; ++l) t->key_order[l] = key_order[l];
     const uint64_t n = rel->nrows;
     const unsigned T = 256;
@@ -837,7 +842,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         }
         // layout decisions on the level arrays as written (upper levels still
         // in their temporaries), set counts read on the device
-        if (s == LH_OK && pol.bs_ratio != 0) {
+        if (s == LH_OK && any_ratio) {
             unsigned long long *d_tot = (unsigned long long *)(d_count + L + 1);
             for (uint32_t l = 0; l < L && s == LH_OK; ++l) {
                 const uint64_t cap_sets = l ? n : 1;
@@ -847,7 +852,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
                 const uint32_t *lv_vals = l + 1 < L ? tvals[l] : t->lv[l].vals;
                 const uint32_t *poffs = l ? toffs[l - 1] : nullptr;
                 LH_TRACED(ctx, "k_layout_decide", k_layout_decide<<<lh_blocks(cap_sets, T, (uint32_t)ctx->num_sms * 16), T, 0, ctx->stream>>>(
-                    lv_vals, poffs, 1, 0, l ? d_count + (l - 1) : nullptr, d_count + l, pol.bs_ratio,
+                    lv_vals, poffs, 1, 0, l ? d_count + (l - 1) : nullptr, d_count + l, t->level_ratio[l],
                     pol.bs_min_card, pre.isbs[l], pre.words[l], d_tot + 2 * l));
             }
         }
@@ -927,7 +932,7 @@ extern "C" lh_status lh_build_trie(lh_ctx *ctx, const lh_relation_desc *rel,
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "build_trie: %s", cudaGetErrorString(e));
     }
     cleanup_tmp();
-    if (s == LH_OK && n && pol.bs_ratio != 0) s = trie_layout(ctx, t, &pre);
+    if (s == LH_OK && n && any_ratio) s = trie_layout(ctx, t, &pre);
     else STEP(lh_trie_layout(ctx, t));
     free_pre();
 #undef STEP
@@ -967,6 +972,7 @@ extern "C" lh_status lh_filter_trie(lh_ctx *ctx, const int32_t *col, uint64_t n,
     t->key_bits[0] = n > 1 ? 64 - __builtin_clzll(n - 1) : 1;
     t->bs_ratio = pol.bs_ratio;
     t->bs_min_card = pol.bs_min_card;
+    t->level_ratio[0] = pol.per_level ? pol.level_ratio[0] : pol.bs_ratio;
     const unsigned T = 256;
     const unsigned G = (unsigned)std::min<uint64_t>(lh_blocks(n, T), (uint64_t)ctx->num_sms * 16);
     const unsigned G4 = (unsigned)std::min<uint64_t>(lh_blocks((n + 3) / 4, T), (uint64_t)ctx->num_sms * 16);

@@ -56,10 +56,21 @@ class Hypergraph:
 
 # ------------------------------------------------------- fractional covers
 
+_RHO = {}
+
+
 def rho_star(bag, edges) -> float:
     """Fractional edge cover number of the vertex set `bag`: the minimum of
     sum_e x_e subject to sum_{e contains v} x_e >= 1 for every v in bag and
-    x >= 0 (the width measure of a GHD node, Section 2.3)."""
+    x >= 0 (the width measure of a GHD node, Section 2.3).  Memoised: a
+    plan search asks for the same bags many times."""
+    key = (frozenset(bag), tuple(tuple(e) for e in edges))
+    if key not in _RHO:
+        _RHO[key] = _rho_star(bag, edges)
+    return _RHO[key]
+
+
+def _rho_star(bag, edges) -> float:
     bag = sorted(bag)
     if not bag:
         return 0.0

@@ -21,7 +21,7 @@ MAX_LEVELS = 6
 MAX_ATTRS = 6
 MAX_EDGES = 8
 MAX_ANNOS = 4
-NFEAT = 60
+NFEAT = 64
 MAX_GROUP = 6
 GROUP_AUTO, GROUP_DENSE, GROUP_PRIVATE, GROUP_SHARED = 0, 1, 2, 3
 
@@ -57,7 +57,26 @@ class RowFilter(C.Structure):
 
 
 class LayoutPolicy(C.Structure):
-    _fields_ = [("bs_ratio", C.c_uint32), ("bs_min_card", C.c_uint32)]
+    _fields_ = [("bs_ratio", C.c_uint32), ("bs_min_card", C.c_uint32), ("per_level", C.c_uint32),
+                ("level_ratio", C.c_uint32 * MAX_LEVELS)]
+
+
+def layout_policy(layout):
+    """LayoutPolicy from (ratio, min_card) -- one ratio for every level -- or
+    (level-0 ratio, inner-level ratio, min_card) -- a ratio per level."""
+    if len(layout) == 2:
+        return LayoutPolicy(int(layout[0]), int(layout[1]))
+    pol = LayoutPolicy(int(layout[0]), int(layout[2]), 1)
+    pol.level_ratio[0] = int(layout[0])
+    for l in range(1, MAX_LEVELS):
+        pol.level_ratio[l] = int(layout[1])
+    return pol
+
+
+def plan_layout(plan):
+    """The per-level layout a plan's tries are built with."""
+    r0, r1 = int(plan.bs_ratio), int(plan.bs_ratio_inner)
+    return (r0, r1, 32 if (r0 or r1) else 0)
 
 
 class TrieStats(C.Structure):
@@ -96,7 +115,7 @@ class Query(C.Structure):
 class Plan(C.Structure):
     _fields_ = [("n_attrs", C.c_uint32), ("order", C.c_uint32 * MAX_ATTRS), ("bs_ratio", C.c_uint32),
                 ("exec", C.c_uint32), ("cost", C.c_int64), ("predicted_log_ms", C.c_float),
-                ("measured_ms", C.c_float), ("n_candidates", C.c_uint32)]
+                ("measured_ms", C.c_float), ("n_candidates", C.c_uint32), ("bs_ratio_inner", C.c_uint32)]
 
     def order_list(self):
         return [int(self.order[i]) for i in range(self.n_attrs)]
@@ -104,7 +123,7 @@ class Plan(C.Structure):
 
 class PlanOpts(C.Structure):
     _fields_ = [("n_policies", C.c_uint32), ("policies", C.c_uint32 * 4),
-                ("time_budget_ms", C.c_float), ("repeats", C.c_uint32)]
+                ("time_budget_ms", C.c_float), ("repeats", C.c_uint32), ("per_level", C.c_uint32)]
 
 
 class ResultView(C.Structure):
@@ -305,7 +324,7 @@ class Context:
         order = (C.c_uint32 * MAX_LEVELS)(*(key_order if key_order is not None else range(len(keys))))
         pol = None
         if layout is not None:
-            pol = LayoutPolicy(*layout)
+            pol = layout_policy(layout)
         out = C.c_void_p()
         if where:
             filt = (RowFilter * len(where))(*[RowFilter(c.data_ptr(), int(lo), int(hi)) for c, lo, hi in where])
@@ -323,14 +342,14 @@ class Context:
         the fp32 (high, low) pair of each tuple's aggregate."""
         arr = (C.c_void_p * max(1, len(tries)))(*[t.h.value for t in tries])
         oa = (C.c_uint32 * len(out_attrs))(*out_attrs)
-        pol = LayoutPolicy(*layout) if layout is not None else None
+        pol = layout_policy(layout) if layout is not None else None
         out = C.c_void_p()
         self._check(lib().lh_join_to_trie(self.h, C.byref(q), C.byref(plan), arr, len(out_attrs), oa,
                                           C.byref(pol) if pol is not None else None, C.byref(out)))
         return Trie(self, out)
 
     def filter_trie(self, col, lo, hi, layout=None):
-        pol = LayoutPolicy(*layout) if layout is not None else None
+        pol = layout_policy(layout) if layout is not None else None
         out = C.c_void_p()
         self._check(lib().lh_filter_trie(self.h, _ptr(col), int(col.numel()), int(lo), int(hi),
                                          C.byref(pol) if pol is not None else None, C.byref(out)))
@@ -536,12 +555,13 @@ def make_query(n_attrs, edges, semiring=COUNT_U64, group=(), materialized=(), eq
     return q
 
 
-def make_plan(order, bs_ratio=32, exec_kind=EXEC_AUTO):
+def make_plan(order, bs_ratio=32, exec_kind=EXEC_AUTO, bs_ratio_inner=None):
     p = Plan()
     p.n_attrs = len(order)
     for i, a in enumerate(order):
         p.order[i] = a
     p.bs_ratio = bs_ratio
+    p.bs_ratio_inner = bs_ratio if bs_ratio_inner is None else bs_ratio_inner
     p.exec = exec_kind
     p.cost = -1
     p.predicted_log_ms = math.nan
@@ -593,7 +613,7 @@ class GraphJoin:
 
     def time_plan(self, plan, budget_ms=0.0, repeats=1):
         """Engine-measured ms of this query under plan (None if over budget)."""
-        tries, q = self._bind(plan, (plan.bs_ratio, 32 if plan.bs_ratio else 0))
+        tries, q = self._bind(plan, plan_layout(plan))
         arr = (C.c_void_p * max(1, len(tries)))(*[t.h.value for t in tries])
         ms = C.c_float()
         st = lib().lh_plan_time(self.ctx.h, C.byref(q), C.byref(plan), arr, budget_ms, repeats, C.byref(ms))
@@ -603,7 +623,7 @@ class GraphJoin:
         return float(ms.value)
 
     def features(self, plan):
-        tries, q = self._bind(plan, (plan.bs_ratio, 32 if plan.bs_ratio else 0))
+        tries, q = self._bind(plan, plan_layout(plan))
         return plan_features(self.ctx, q, plan, tries)
 
     def _bind(self, plan, layout=None):
@@ -881,8 +901,9 @@ def plan_features(ctx, q, plan, tries):
     return np.array(f[:], dtype=np.float32)
 
 
-def plan_opts(policies=(0, 8, 32, 128), budget_ms=0.0, repeats=1):
+def plan_opts(policies=(0, 8, 32, 128), budget_ms=0.0, repeats=1, per_level=False):
     o = PlanOpts()
+    o.per_level = 1 if per_level else 0
     o.n_policies = len(policies)
     for i, p in enumerate(policies):
         o.policies[i] = p

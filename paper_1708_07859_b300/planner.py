@@ -27,12 +27,15 @@ from . import lh
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "models", "planner_mlp.npy")
 TEMPLATES = ("triangle", "clique4", "cycle4", "lollipop", "path3", "star3")
-POLICIES = (0, 32)
+# layout ratios per trie level: uint only, or bitsets for sets at least 1/8,
+# 1/32, 1/128 dense; a plan takes one for level 0 and one for the deeper levels
+POLICIES = (0, 8, 32, 128)
+JUDGE_POLICIES = (0, 32)      # the exhaustive judge's per-level grid (4 layouts)
 TRAIN_SEED = gen.SEED_BASE + 5000     # disjoint from the evaluation seeds below
 EVAL_SEED = gen.SEED_BASE + 5
 
 
-def random_graph(rng, m_lo=2 ** 10, m_hi=2 ** 18):
+def random_graph(rng, m_lo=2 ** 10, m_hi=2 ** 20):
     """G(n, m) or Chung-Lu (beta in [2, 3]) with log-uniform edge count."""
     m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
     seed = int(rng.integers(0, 2 ** 31))
@@ -44,35 +47,64 @@ def random_graph(rng, m_lo=2 ** 10, m_hi=2 ** 18):
     return gen.chung_lu_edges(n, m, beta, seed), ("chung_lu", n, m, beta)
 
 
-def plan_for(order, ratio):
-    return lh.make_plan(list(order), bs_ratio=ratio)
+def plan_for(order, ratio, inner=None):
+    return lh.make_plan(list(order), bs_ratio=ratio, bs_ratio_inner=inner)
 
 
-def generate_training(ctx, n_queries, seed=TRAIN_SEED, plans_per_query=8, budget_ms=200.0, log=None):
-    """(X, y, meta): features of sampled (query, plan) pairs and the log of
-    their measured ms.  Plans over the budget are recorded at the budget."""
+def _graph_job(args):
+    seed, = args
     rng = np.random.default_rng(seed)
+    return random_graph(rng)
+
+
+def training_graphs(n_graphs, seed=TRAIN_SEED, workers=0):
+    """Seeded random graphs for the training queries, drawn by spawned worker
+    processes (each graph from its own seed)."""
+    seeds = [(int(x),) for x in np.random.default_rng(seed).integers(0, 2 ** 31, size=n_graphs)]
+    w = workers or (os.cpu_count() or 1)
+    if w <= 1:
+        return [_graph_job(a) for a in seeds]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(w, 32)) as pool:
+        return pool.map(_graph_job, seeds, chunksize=4)
+
+
+def generate_training(ctx, n_queries, seed=TRAIN_SEED, plans_per_query=4, budget_ms=50.0, log=None):
+    """(X, y, meta): features of sampled (query, plan) pairs and the log of
+    their engine-measured ms.  Every graph serves all six templates (one
+    query each); a query's plans are its cost-model plan plus random
+    (order, level-0 layout, inner layout) samples.  Plans over the budget are
+    recorded at the budget."""
+    rng = np.random.default_rng(seed + 1)
+    n_graphs = (n_queries + len(TEMPLATES) - 1) // len(TEMPLATES)
+    graphs = training_graphs(n_graphs, seed)
     X, y, meta = [], [], []
     t0 = time.time()
-    for qi in range(n_queries):
-        shape = TEMPLATES[qi % len(TEMPLATES)]
-        (s, d), gdesc = random_graph(rng)
-        g = lh.GraphJoin(ctx, lh.to_device_u32(s), lh.to_device_u32(d), shape)
-        k = g.n_attrs
-        orders = list(itertools.permutations(range(k)))
-        cand = [(tuple(g.plan().order_list()), 32)]
-        for _ in range(plans_per_query):
-            cand.append((orders[int(rng.integers(len(orders)))], POLICIES[int(rng.integers(len(POLICIES)))]))
-        for order, ratio in dict.fromkeys(cand):
-            p = plan_for(order, ratio)
-            ms = g.time_plan(p, budget_ms=budget_ms)
-            ms = budget_ms if ms is None else ms
-            X.append(g.features(p))
-            y.append(math.log(max(ms, 1e-3)))
-            meta.append({"q": qi, "shape": shape, "graph": gdesc, "order": list(order), "ratio": ratio, "ms": ms})
-        g.free()
-        if log and (qi + 1) % 100 == 0:
-            log(f"{qi + 1}/{n_queries} queries, {len(y)} samples, {time.time() - t0:.0f}s")
+    qi = 0
+    for (s, d), gdesc in graphs:
+        ds, dd = lh.to_device_u32(s), lh.to_device_u32(d)
+        for shape in TEMPLATES:
+            if qi >= n_queries:
+                break
+            g = lh.GraphJoin(ctx, ds, dd, shape)
+            orders = list(itertools.permutations(range(g.n_attrs)))
+            cand = [(tuple(g.plan().order_list()), 32, 32)]
+            for _ in range(plans_per_query):
+                cand.append((orders[int(rng.integers(len(orders)))], POLICIES[int(rng.integers(len(POLICIES)))],
+                             POLICIES[int(rng.integers(len(POLICIES)))]))
+            for order, r0, r1 in dict.fromkeys(cand):
+                p = plan_for(order, r0, r1)
+                ms = g.time_plan(p, budget_ms=budget_ms)
+                ms = budget_ms if ms is None else ms
+                X.append(g.features(p))
+                y.append(math.log(max(ms, 1e-3)))
+                meta.append({"q": qi, "shape": shape, "graph": gdesc, "order": list(order), "layout": [r0, r1],
+                             "ms": ms})
+            g.free()
+            qi += 1
+            if log and qi % 300 == 0:
+                log(f"{qi}/{n_queries} queries, {len(y)} samples, {time.time() - t0:.0f}s")
+        del ds, dd
     return np.stack(X).astype(np.float32), np.asarray(y, dtype=np.float32), meta
 
 
@@ -92,32 +124,43 @@ def load_model(ctx, path=DEFAULT_WEIGHTS, hidden=64):
     return m
 
 
-def compare(ctx, model, shape, src, dst, budget_ms=2000.0, repeats=3):
-    """Plan times of one query: cost model, learned model, exhaustive best,
-    and the counts each plan returned (they must agree)."""
+def compare(ctx, model, shape, src, dst, budget_ms=None, repeats=3, judge=JUDGE_POLICIES):
+    """Plan times of one query: the cost model's plan, the learned model's
+    (every order x per-level layout over POLICIES), and the exhaustive
+    judge's best (every order x per-level layout over `judge`, each run cut
+    at the budget: by default three times the cost plan's time), with the
+    counts each plan returned (they must agree).  best is the fastest plan
+    seen by any of the three; regrets are times over it."""
     g = lh.GraphJoin(ctx, lh.to_device_u32(src), lh.to_device_u32(dst), shape)
     out = {"shape": shape, "edges": int(src.size)}
     t0 = time.perf_counter()
     pc = g.plan()
     out["cost_plan_s"] = time.perf_counter() - t0
+    t_cost = g.time_plan(pc, budget_ms=0.0, repeats=1)
     t0 = time.perf_counter()
-    pl = g.plan(lh.PLANNER_LEARNED, model=model, opts=lh.plan_opts(POLICIES))
+    pl = g.plan(lh.PLANNER_LEARNED, model=model, opts=lh.plan_opts(POLICIES, per_level=True))
     out["learned_plan_s"] = time.perf_counter() - t0
+    budget = budget_ms if budget_ms is not None else max(5.0, 3.0 * t_cost)
     t0 = time.perf_counter()
-    pe = g.plan(lh.PLANNER_EXHAUSTIVE, opts=lh.plan_opts(POLICIES, budget_ms=budget_ms, repeats=1))
+    pe = g.plan(lh.PLANNER_EXHAUSTIVE, opts=lh.plan_opts(judge, budget_ms=budget, repeats=1, per_level=True))
     out["exhaustive_plan_s"] = time.perf_counter() - t0
-    for name, p in (("cost", pc), ("learned", pl), ("best", pe)):
+    out["judge_candidates"] = int(pe.n_candidates)
+    for name, p in (("cost", pc), ("learned", pl), ("judge", pe)):
         ms = g.time_plan(p, budget_ms=0.0, repeats=repeats)
-        cnt, _ = g.run(p, layout=(p.bs_ratio, 32 if p.bs_ratio else 0))
-        out[name] = {"order": p.order_list(), "bs_ratio": int(p.bs_ratio), "ms": ms, "count": cnt}
-    out["identical_counts"] = len({out[k]["count"] for k in ("cost", "learned", "best")}) == 1
+        cnt, _ = g.run(p, layout=lh.plan_layout(p))
+        out[name] = {"order": p.order_list(), "layout": [int(p.bs_ratio), int(p.bs_ratio_inner)], "ms": ms,
+                     "count": cnt}
+    best = min(("cost", "learned", "judge"), key=lambda k: out[k]["ms"])
+    out["best"] = dict(out[best], source=best)
+    out["identical_counts"] = len({out[k]["count"] for k in ("cost", "learned", "judge")}) == 1
     out["regret_learned"] = out["learned"]["ms"] / out["best"]["ms"]
     out["regret_cost"] = out["cost"]["ms"] / out["best"]["ms"]
     g.free()
     return out
 
 
-def eval_graphs(n_graphs=2, m=1 << 22, n=1 << 19, beta=2.1, seed=EVAL_SEED):
+def eval_graphs(n_graphs=5, m=1 << 22, n=1 << 19, beta=2.1, seed=EVAL_SEED):
+    """Held-out evaluation graphs (seeds disjoint from training's)."""
     return [gen.chung_lu_edges(n, m, beta, seed + i) for i in range(n_graphs)]
 
 
@@ -125,13 +168,13 @@ def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     t = sub.add_parser("train")
-    t.add_argument("--queries", type=int, default=2000)
+    t.add_argument("--queries", type=int, default=10000)
     t.add_argument("--epochs", type=int, default=300)
     t.add_argument("--out", default=DEFAULT_WEIGHTS)
     t.add_argument("--log", default=None)
     e = sub.add_parser("eval")
     e.add_argument("--weights", default=DEFAULT_WEIGHTS)
-    e.add_argument("--graphs", type=int, default=2)
+    e.add_argument("--graphs", type=int, default=5)
     e.add_argument("--edges", type=int, default=1 << 22)
     e.add_argument("--out", default=None)
     args = ap.parse_args()

@@ -350,6 +350,8 @@ def plan_and_run(ctx, text, catalog, pushdown=True, single_node=False):
     import numpy as np
 
     from . import ghd, lh
+    import time
+    t_plan = time.perf_counter()
     tr = translate(text, catalog)
     table_of = {a: t for a, t, _ in tr.edges}
     selected = {c.rel for c, _, _ in tr.selections}
@@ -371,6 +373,8 @@ def plan_and_run(ctx, text, catalog, pushdown=True, single_node=False):
     plan = ghd.single_node(hg) if single_node else ghd.choose_ghd(hg, push_selections=pushdown)
     if single_node and pushdown:
         ghd.pushdown(plan, hg)
+    plan.plan_ms = (time.perf_counter() - t_plan) * 1e3
+    t_exec = time.perf_counter()
     rels = []
     for a, t, cols in tr.edges:
         d = catalog[t]["data"]
@@ -403,6 +407,7 @@ def plan_and_run(ctx, text, catalog, pushdown=True, single_node=False):
     ex = ghd.Executor(ctx, lh, hg, rels, semiring)
     gs, gc, view = ex.run(plan, list(zip(group_vertices, cards)), pushdown=pushdown)
     plan.log = ex.log
+    plan.exec_ms = (time.perf_counter() - t_exec) * 1e3
     # dense groups over the key vertices -> requested group keys
     out = {}
     idx = np.flatnonzero(gc)
