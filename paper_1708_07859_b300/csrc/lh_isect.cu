@@ -438,6 +438,12 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
         stage_merge(d, la_buf, lb_buf, &bar, offa, offb);
         uses++;
     }
+    uint32_t xn[kItems];   // uint elements of the next probe / uint-cap-bs tile
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const uint32_t k = threadIdx.x + r * kThreads;
+        xn[r] = ((d.kind & 255u) == K_UBS || (d.kind & 255u) == K_PROBE) && k < d.la ? __ldg(d.a + k) : 0u;
+    }
     while (tile < total) {
         const uint64_t next = tile + gridDim.x;
         TileDesc dnn = dn;
@@ -473,6 +479,19 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
             stage_merge(dn, la_buf, lb_buf, &bar, offa, offb);
             uses++;
         }
+        // a probe / uint-cap-bs tile's uint elements were loaded during the
+        // previous tile (or before the loop); the next tile's are issued
+        // now, so they arrive while this tile is counted
+        uint32_t x[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) x[r] = xn[r];
+        if (next < total && ((dn.kind & 255u) == K_UBS || (dn.kind & 255u) == K_PROBE)) {
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                xn[r] = k < dn.la ? __ldg(dn.a + k) : 0u;
+            }
+        }
         uint32_t cnt = 0;
         if (kind == K_MERGE) {
             const uint32_t s = threadIdx.x * kItems;
@@ -492,12 +511,6 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
                 }
             }
         } else if (kind == K_UBS || kind == K_PROBE) {
-            uint32_t x[kItems];
-#pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const uint32_t k = threadIdx.x + r * kThreads;
-                x[r] = k < la ? __ldg(d.a + k) : 0u;
-            }
             if (kind == K_UBS) {
                 uint32_t w[kItems];
 #pragma unroll
@@ -524,13 +537,23 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
                 }
             }
         } else if (kind == K_BB) {
+            // a tile is at most kTile words = kTile / 4 16-byte vectors per
+            // side: every load of the thread is issued before the ANDs
             const uint4 *qa = (const uint4 *)d.a;
             const uint4 *qb = (const uint4 *)d.b;
             const uint32_t nv = la >> 2;
-            for (uint32_t k = threadIdx.x; k < nv; k += kThreads) {
-                const uint4 xx = __ldg(qa + k), yy = __ldg(qb + k);
-                cnt += __popc(xx.x & yy.x) + __popc(xx.y & yy.y) + __popc(xx.z & yy.z) + __popc(xx.w & yy.w);
+            constexpr int kVec = kTile / 4 / kThreads;
+            uint4 xa[kVec], xb[kVec];
+#pragma unroll
+            for (int u = 0; u < kVec; ++u) {
+                const uint32_t k = threadIdx.x + u * kThreads;
+                xa[u] = k < nv ? __ldg(qa + k) : make_uint4(0, 0, 0, 0);
+                xb[u] = k < nv ? __ldg(qb + k) : make_uint4(0, 0, 0, 0);
             }
+#pragma unroll
+            for (int u = 0; u < kVec; ++u)
+                cnt += __popc(xa[u].x & xb[u].x) + __popc(xa[u].y & xb[u].y) + __popc(xa[u].z & xb[u].z) +
+                       __popc(xa[u].w & xb[u].w);
         }
         const uint32_t tot = block_sum(cnt, red);  // ends with a barrier: the padded tile is free again
         if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + d.pair), (unsigned long long)tot);

@@ -27,6 +27,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr uint32_t kSmemGroupsMax = 1024;
+constexpr uint64_t kLastChunk = 1ull << 28;   // candidates per last-attribute launch
 constexpr int kMaxG = LH_MAX_GROUP;
 constexpr uint32_t kPrivSlots = 256;                 // per-warp private GROUP BY table
 constexpr unsigned long long kPrivEmpty = ~0ull;
@@ -546,12 +547,25 @@ struct Driver {
                 o.gsum = r->d_gsum;
                 o.gcount = (unsigned long long *)r->d_gcount;
                 o.status = ctx->d_status;
-                if (mode_last == M_COUNT)
-                    LH_TRACED(ctx, "k_expand", k_expand<M_COUNT><<<grid_expand, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o));
-                else
-                    LH_TRACED(ctx, "k_expand", k_expand<M_AGG><<<grid_expand, kThreads, smem_bytes, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, 0, total, o));
-                cudaError_t e = cudaGetLastError();
-                if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e));
+                // the last attribute's candidates in launches of at most
+                // kLastChunk, so that a time budget can stop a join whose
+                // frontier fans out into billions of candidates
+                for (uint64_t c0 = 0; c0 < total && s == LH_OK; c0 += kLastChunk) {
+                    if (c0) s = check_time();
+                    if (s != LH_OK) break;
+                    const uint64_t c1 = std::min<uint64_t>(total, c0 + kLastChunk);
+                    if (mode_last == M_COUNT)
+                        LH_TRACED(ctx, "k_expand", k_expand<M_COUNT><<<grid_expand, kThreads, 0, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, c0, c1, o));
+                    else
+                        LH_TRACED(ctx, "k_expand", k_expand<M_AGG><<<grid_expand, kThreads, smem_bytes, ctx->stream>>>(q, d, posF, gvF, nF, capF, off, drvb, c0, c1, o));
+                    cudaError_t e = cudaGetLastError();
+                    if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e));
+                    if (s == LH_OK && deadline_ms > 0 && c1 < total) {
+                        // the host clock only sees the time once the work is done
+                        cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+                        if (e2 != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e2));
+                    }
+                }
             }
         } else if (s == LH_OK) {
             for (uint64_t c0 = 0; c0 < total && s == LH_OK; c0 += cap) {

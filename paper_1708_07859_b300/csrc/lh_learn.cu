@@ -488,6 +488,24 @@ lh_status lh_plan_exhaustive(lh_ctx *ctx, const lh_query *q, const lh_relation_d
                              const lh_plan_opts *o, lh_plan_t *out) {
     std::vector<std::vector<uint32_t>> orders;
     lh_candidate_orders(q, orders);
+    // candidates in the order of the Section 4 cost estimate, so that fast
+    // plans come early; each later run is cut once it takes 1.25x the best
+    // time seen so far (it cannot be the fastest), which keeps the judge
+    // exhaustive while bounding the time spent on hopeless plans
+    {
+        uint64_t cards[LH_MAX_EDGES];
+        for (uint32_t e = 0; e < q->n_edges; ++e) {
+            uint64_t c = q->edges[e].card;
+            if (!c && q->edges[e].trie_slot < 0) c = q->edges[e].flat_n;
+            if (!c && rels && rels[e]) c = rels[e]->nrows;
+            cards[e] = c ? c : 1;
+        }
+        int64_t w[LH_MAX_ATTRS] = {0};
+        lh_weights(q, cards, w);
+        std::stable_sort(orders.begin(), orders.end(), [&](const std::vector<uint32_t> &x, const std::vector<uint32_t> &y) {
+            return lh_cost_of(q, x.data(), w) < lh_cost_of(q, y.data(), w);
+        });
+    }
     TrieCache cache{ctx, {}};
     const lh_query qs = with_edge_slots(q);
     cudaEvent_t e0, e1;
@@ -513,10 +531,12 @@ lh_status lh_plan_exhaustive(lh_ctx *ctx, const lh_query *q, const lh_relation_d
             double tot = 0;
             bool timed_out = false;
             const uint32_t reps = std::max<uint32_t>(1, o->repeats);
+            double cut = budget;
+            if (best_ms < 1e299) cut = cut > 0 ? std::min(cut, 1.25 * best_ms) : 1.25 * best_ms;
             for (uint32_t r = 0; r <= reps; ++r) {  // first run warms up
                 lh_result *res = nullptr;
                 cudaEventRecord(e0, ctx->stream);
-                lh_status st = lh_join_dispatch(ctx, &qs, &p, tr, &res, budget);
+                lh_status st = lh_join_dispatch(ctx, &qs, &p, tr, &res, cut);
                 cudaEventRecord(e1, ctx->stream);
                 if (st == LH_ETIMEOUT) {
                     timed_out = true;

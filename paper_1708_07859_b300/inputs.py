@@ -165,9 +165,12 @@ def batch_graphs(count: int = 4096, seed_offset: int = 4, workers: int = 0):
     w = workers or (os.cpu_count() or 1)
     if w <= 1 or count < 64:
         return [batch_graph(*a) for a in args]
+    import concurrent.futures as cf
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(min(w, 32)) as pool:
-        return pool.map(_batch_graph_args, args, chunksize=32)
+    # fresh interpreters (a forked CUDA process would hang); a worker that
+    # dies raises BrokenProcessPool here instead of leaving the map waiting
+    with cf.ProcessPoolExecutor(min(w, 32), mp_context=mp.get_context("spawn")) as pool:
+        return list(pool.map(_batch_graph_args, args, chunksize=32, timeout=1800))
 
 
 HUB_GRAPH = (1 << 20, 1 << 24, 2.1)   # n, m, degree exponent of the power-law batch graph

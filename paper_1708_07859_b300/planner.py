@@ -59,14 +59,19 @@ def _graph_job(args):
 
 def training_graphs(n_graphs, seed=TRAIN_SEED, workers=0):
     """Seeded random graphs for the training queries, drawn by spawned worker
-    processes (each graph from its own seed)."""
+    processes (each graph from its own seed).  A script calling this must
+    guard its entry point with ``if __name__ == "__main__"`` (spawned
+    workers import the main module)."""
     seeds = [(int(x),) for x in np.random.default_rng(seed).integers(0, 2 ** 31, size=n_graphs)]
     w = workers or (os.cpu_count() or 1)
     if w <= 1:
         return [_graph_job(a) for a in seeds]
+    import concurrent.futures as cf
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(min(w, 32)) as pool:
-        return pool.map(_graph_job, seeds, chunksize=4)
+    # fresh interpreters (a forked CUDA process would hang); a worker that
+    # dies raises BrokenProcessPool here instead of leaving the map waiting
+    with cf.ProcessPoolExecutor(min(w, 32), mp_context=mp.get_context("spawn")) as pool:
+        return list(pool.map(_graph_job, seeds, chunksize=4, timeout=3600))
 
 
 def generate_training(ctx, n_queries, seed=TRAIN_SEED, plans_per_query=4, budget_ms=50.0, log=None):
