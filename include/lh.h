@@ -73,6 +73,26 @@ typedef struct lh_batch lh_batch;
  * and freed on that stream); the pool keeps freed memory for reuse until
  * lh_destroy. */
 lh_status lh_create(lh_ctx **out, void *cuda_stream);
+
+/* Device memory from the caller's allocator instead of the context's pool
+ * (for an application whose framework owns the GPU's memory, e.g. a
+ * caching allocator).  alloc returns `bytes` of device memory usable by work
+ * issued on `cuda_stream` after the call (NULL on failure: the library call
+ * then returns LH_ENOMEM); free releases a pointer the library no longer
+ * needs, possibly while work that reads it is still queued on the stream, so
+ * the memory may only be reused by work ordered after that (the semantics of
+ * a stream-ordered or single-stream caching allocator).  user is passed
+ * through unchanged. */
+typedef struct {
+    void *(*alloc)(uint64_t bytes, void *cuda_stream, void *user);
+    void (*free)(void *ptr, void *cuda_stream, void *user);
+    void *user;
+} lh_alloc_fns;
+
+/* lh_create with the caller's allocator for every device allocation of the
+ * context (fns copied; alloc and free must be non-NULL).  lh_pool_reserve
+ * and lh_pool_usage then return LH_EUNSUPPORTED. */
+lh_status lh_create_with_allocator(lh_ctx **out, void *cuda_stream, const lh_alloc_fns *fns);
 lh_status lh_destroy(lh_ctx *ctx);
 lh_status lh_set_stream(lh_ctx *ctx, void *cuda_stream);
 /* Maps `bytes` of device memory into the context's pool up front (one

@@ -18,15 +18,19 @@ static void trace_fold(lh_ctx *ctx);
 
 extern "C" const char *lh_version(void) { return "lh-b300 0.1 (sm_103a)"; }
 
-extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
+static lh_status create_ctx(lh_ctx **out, void *stream, const lh_alloc_fns *fns) {
     if (!out) return LH_EINVAL;
     *out = nullptr;
     lh_ctx *ctx = new lh_ctx();
     ctx->stream = (cudaStream_t)stream;
+    if (fns) {
+        ctx->user_alloc = true;
+        ctx->fns = *fns;
+    }
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !fns) {
         // a private pool whose memory stays mapped between calls: the default
         // pool would hand multi-GB temporaries back at every synchronisation
         cudaMemPoolProps props;
@@ -41,14 +45,25 @@ extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
             e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_status, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) {
+        if (fns) {
+            ctx->d_status = (uint32_t *)fns->alloc(sizeof(uint32_t), stream, fns->user);
+            if (!ctx->d_status) e = cudaErrorMemoryAllocation;
+        } else {
+            e = cudaMalloc((void **)&ctx->d_status, sizeof(uint32_t));
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess)
         e = cudaHostAlloc((void **)&ctx->h_pinned, lh_ctx::kPinnedWords * sizeof(uint64_t),
                           cudaHostAllocDefault);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->d_status) {
+            if (fns) fns->free(ctx->d_status, stream, fns->user);
+            else cudaFree(ctx->d_status);
+        }
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         delete ctx;
         return LH_ECUDA;
@@ -57,12 +72,22 @@ extern "C" lh_status lh_create(lh_ctx **out, void *stream) {
     return LH_OK;
 }
 
+extern "C" lh_status lh_create(lh_ctx **out, void *stream) { return create_ctx(out, stream, nullptr); }
+
+extern "C" lh_status lh_create_with_allocator(lh_ctx **out, void *stream, const lh_alloc_fns *fns) {
+    if (!fns || !fns->alloc || !fns->free) return LH_EINVAL;
+    return create_ctx(out, stream, fns);
+}
+
 extern "C" lh_status lh_destroy(lh_ctx *ctx) {
     if (!ctx) return LH_EINVAL;
     cudaStreamSynchronize(ctx->stream);
     trace_fold(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_status) {
+        if (ctx->user_alloc) ctx->fns.free(ctx->d_status, (void *)ctx->stream, ctx->fns.user);
+        else cudaFree(ctx->d_status);
+    }
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->pool) {
         cudaDeviceSynchronize();  // memory freed asynchronously must be released before the pool goes
@@ -73,7 +98,9 @@ extern "C" lh_status lh_destroy(lh_ctx *ctx) {
 }
 
 extern "C" lh_status lh_pool_reserve(lh_ctx *ctx, uint64_t bytes) {
-    if (!ctx || !ctx->pool) return LH_EINVAL;
+    if (!ctx) return LH_EINVAL;
+    if (ctx->user_alloc) return lh_fail(ctx, LH_EUNSUPPORTED, "the context uses the caller's allocator");
+    if (!ctx->pool) return LH_EINVAL;
     if (bytes == 0) return LH_OK;
     void *p = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, ctx->pool, ctx->stream);
@@ -88,7 +115,9 @@ extern "C" lh_status lh_pool_reserve(lh_ctx *ctx, uint64_t bytes) {
 }
 
 extern "C" lh_status lh_pool_usage(lh_ctx *ctx, uint64_t *used_now, uint64_t *used_high, int reset_high) {
-    if (!ctx || !ctx->pool) return LH_EINVAL;
+    if (!ctx) return LH_EINVAL;
+    if (ctx->user_alloc) return lh_fail(ctx, LH_EUNSUPPORTED, "the context uses the caller's allocator");
+    if (!ctx->pool) return LH_EINVAL;
     unsigned long long now = 0, high = 0;  // the pool attributes are 64-bit
     LH_CU(cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &now));
     LH_CU(cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &high));

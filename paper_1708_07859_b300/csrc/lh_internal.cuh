@@ -31,6 +31,8 @@ struct lh_ctx {
     int num_sms = 148;
     std::string err;
     cudaMemPool_t pool = nullptr;   // private stream-ordered pool (keeps its memory)
+    bool user_alloc = false;        // device memory through the caller's allocator
+    lh_alloc_fns fns{};
     uint32_t *d_status = nullptr;   // first device-side error (lh_status), 0 = none
     uint64_t *h_pinned = nullptr;   // pinned host words for small read-backs
     static constexpr int kPinnedWords = 64;
@@ -80,6 +82,11 @@ template <class T>
 static inline lh_status lh_alloc(lh_ctx *ctx, T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (ctx->user_alloc) {
+        *p = (T *)ctx->fns.alloc((uint64_t)(count * sizeof(T)), (void *)ctx->stream, ctx->fns.user);
+        if (!*p) return lh_fail(ctx, LH_ENOMEM, "caller's allocator refused %zu bytes", count * sizeof(T));
+        return LH_OK;
+    }
     cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync((void **)p, count * sizeof(T), ctx->pool, ctx->stream)
                               : cudaMallocAsync((void **)p, count * sizeof(T), ctx->stream);
     if (e != cudaSuccess) {
@@ -90,7 +97,9 @@ static inline lh_status lh_alloc(lh_ctx *ctx, T **p, size_t count) {
     return LH_OK;
 }
 static inline void lh_free(lh_ctx *ctx, void *p) {
-    if (p) cudaFreeAsync(p, ctx->stream);
+    if (!p) return;
+    if (ctx->user_alloc) ctx->fns.free(p, (void *)ctx->stream, ctx->fns.user);
+    else cudaFreeAsync(p, ctx->stream);
 }
 
 // Copy `n` 64-bit device words to the pinned buffer and wait for them.

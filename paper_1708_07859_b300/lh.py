@@ -152,6 +152,7 @@ class BatchTuning(C.Structure):
 
 EXPORTS = {
     "lh_create": [C.c_void_p, C.c_void_p],
+    "lh_create_with_allocator": [C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_destroy": [C.c_void_p],
     "lh_set_stream": [C.c_void_p, C.c_void_p],
     "lh_sync": [C.c_void_p],
@@ -245,17 +246,51 @@ def u32_to_numpy(t):
 
 # ----------------------------------------------------------------- objects
 
-class Context:
-    """An lh_ctx bound to the current torch CUDA stream (or ``stream``)."""
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
-    def __init__(self, stream=None):
+
+class AllocFns(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+def torch_allocator_fns():
+    """lh_alloc_fns that take device memory from torch's caching allocator
+    (stream-ordered on the stream the library passes)."""
+    torch = _torch()
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except RuntimeError:
+            return None
+
+    def free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return AllocFns(ALLOC_FN(alloc), FREE_FN(free), None)
+
+
+class Context:
+    """An lh_ctx bound to the current torch CUDA stream (or ``stream``).
+    allocator="torch" takes every device allocation from torch's caching
+    allocator (lh_create_with_allocator) instead of the context's own pool."""
+
+    def __init__(self, stream=None, allocator=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("liblh needs a CUDA device; there is no CPU fallback")
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.h = C.c_void_p()
-        self._check(lib().lh_create(C.byref(self.h), C.c_void_p(s.cuda_stream)))
+        if allocator is None:
+            self._check(lib().lh_create(C.byref(self.h), C.c_void_p(s.cuda_stream)))
+        else:
+            if allocator != "torch":
+                raise ValueError("allocator: None or 'torch'")
+            self._fns = torch_allocator_fns()   # kept alive with the context
+            self._check(lib().lh_create_with_allocator(C.byref(self.h), C.c_void_p(s.cuda_stream),
+                                                       C.byref(self._fns)))
 
     def _check(self, st):
         if st != OK:
