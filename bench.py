@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the planner and batched-launch comparisons")
     ap.add_argument("--extras-only", action="store_true", help="run only the WCOJ extras (no headline step)")
     ap.add_argument("--only", default="", help="comma list of extras to run alone: triangle, star, batched, "
-                                               "planner, ghd, dense_mv, fig4a")
+                                               "planner, ghd, dense_mv, groupby_key, fig4a")
     return ap.parse_args()
 
 
@@ -378,6 +378,48 @@ def dense_mv(ctx, lh, hbm_peak, l2, n=16384, reps=10):
     torch.cuda.empty_cache()
     return {"n": n, "ms": ms, "alg_bytes": alg, "gb_s": alg / (ms / 1e3) / 1e9,
             "frac_hbm": alg / (ms / 1e3) / 1e9 / hbm_peak, "gflop_s": 2.0 * n * n / (ms / 1e3) / 1e9}
+
+
+def groupby_key(ctx, lh, rows=1 << 17, per_row=32, reps=5):
+    """Figure 5a shape (Section 5, GROUP BY key): C = A B for banded A and B
+    (per_row entries per row; B's band width sets how densely a row of C
+    fills its column span), with the union's GROUP BY key run as bitset +
+    dense array and as sort / hash, timed per SpGEMM (events around the join
+    through its result); both must give the same C."""
+    import torch
+    from paper_1708_07859_b300 import inputs as gen
+    out = {"rows": rows, "per_row": per_row, "cases": []}
+    A = gen.banded_coo(rows, rows, per_row, 128, gen.SEED_BASE + 30)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ta = lh.matrix_trie(ctx, lh.to_device_u32(A[0]), lh.to_device_u32(A[1]), dev(A[2]), dims=(rows, rows))
+    for width in (128, 512, 2048, 8192):
+        B = gen.banded_coo(rows, rows, per_row, width, gen.SEED_BASE + 31)
+        tb = lh.matrix_trie(ctx, lh.to_device_u32(B[0]), lh.to_device_u32(B[1]), dev(B[2]), dims=(rows, rows))
+        rec = {"b_band": width}
+        nnz = {}
+        for name, gi in (("bitset_dense_array", lh.GROUP_DENSE), ("sort_hash", lh.GROUP_PRIVATE)):
+            q = lh.spgemm_query(int(A[0].size), int(B[0].size), gi)
+            plan = lh.make_plan([0, 1, 2])
+            r = ctx.join_aggregate(q, plan, [ta, tb])
+            nnz[name] = int(r.wait().nnz)
+            r.free()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                r = ctx.join_aggregate(q, plan, [ta, tb])
+                r.wait()
+                r.free()
+            e1.record()
+            torch.cuda.synchronize()
+            rec[name + "_ms"] = e0.elapsed_time(e1) / reps
+        rec["nnz_c"] = nnz["sort_hash"]
+        rec["same_nnz"] = nnz["sort_hash"] == nnz["bitset_dense_array"]
+        rec["output_density"] = nnz["sort_hash"] / (rows * (128 + width))
+        out["cases"].append(rec)
+        tb.free()
+    ta.free()
+    return out
 
 
 def triangle_wcoj(ctx, lh, reps=50):
@@ -721,7 +763,8 @@ def wcoj_extras(ctx, lh, hbm, l2):
     and the planner comparison."""
     return {"triangle": triangle_wcoj(ctx, lh), "star": star_join(ctx, lh, hbm),
             "batched": batched_compare(ctx, lh, hbm, l2), "planner": planner_compare(ctx, lh),
-            "ghd": ghd_compare(ctx, lh), "dense_mv": dense_mv(ctx, lh, hbm, l2)}
+            "ghd": ghd_compare(ctx, lh), "dense_mv": dense_mv(ctx, lh, hbm, l2),
+            "groupby_key": groupby_key(ctx, lh)}
 
 
 def main():
@@ -742,6 +785,7 @@ def main():
         run = {"triangle": lambda: triangle_wcoj(ctx, lh), "star": lambda: star_join(ctx, lh, hbm),
                "batched": lambda: batched_compare(ctx, lh, hbm, l2), "planner": lambda: planner_compare(ctx, lh),
                "ghd": lambda: ghd_compare(ctx, lh), "dense_mv": lambda: dense_mv(ctx, lh, hbm, l2),
+               "groupby_key": lambda: groupby_key(ctx, lh),
                "fig4a": lambda: intersect_fig4a(ctx, lh, hbm, l2)}
         print(json.dumps({k: run[k]() for k in args.only.split(",")}))
         ctx.close()

@@ -888,7 +888,13 @@ lh_status lh_join_dispatch(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan
         }
     } else if (exec == LH_EXEC_SPGEMM) {
         if (!is_spgemm(q, plan)) s = lh_fail(ctx, LH_EINVAL, "query is not an SpGEMM join-aggregate under this plan");
-        else s = lh_run_spgemm(ctx, tries[q->edges[0].trie_slot], tries[q->edges[1].trie_slot], r);
+        else {
+            // GROUP BY key implementation (Section 5): group_impl DENSE forces
+            // the bitset + dense array wherever it fits, PRIVATE / SHARED keep
+            // sort and hash, AUTO applies the density rule
+            const uint32_t dm = q->group_impl == LH_GROUP_DENSE ? 2u : q->group_impl == LH_GROUP_AUTO ? 1u : 0u;
+            s = lh_run_spgemm(ctx, tries[q->edges[0].trie_slot], tries[q->edges[1].trie_slot], r, dm);
+        }
     } else {
         s = lh_run_generic(ctx, q, plan, tries, r, deadline_ms);
     }

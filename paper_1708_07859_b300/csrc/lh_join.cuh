@@ -45,7 +45,9 @@ static inline lh_status res_alloc(lh_ctx *ctx, lh_result *r, T **p, size_t count
 // f32 annotation; b: trie of B with levels (j, k) and one f32 annotation.
 lh_status lh_run_spmv(lh_ctx *ctx, const lh_trie *a, const float *x, uint64_t x_n, uint64_t nrows,
                       lh_result *r);
-lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_result *r);
+// dense_mode: 0 never the dense-array GROUP BY key, 1 by the density rule,
+// 2 every row whose output span fits it
+lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_result *r, uint32_t dense_mode);
 
 // Generic attribute-at-a-time driver (lh_join.cu).
 lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,

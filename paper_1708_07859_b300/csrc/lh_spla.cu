@@ -122,22 +122,164 @@ __global__ void k_spgemm_sizes(const uint64_t *u_end, unsigned long long *sizes)
     }
 }
 
-__global__ void k_spgemm_gcap(const uint32_t *ub, const uint32_t *aoffs, uint32_t n, uint64_t *gcap,
-                              unsigned long long *n_hash_rows) {
-    unsigned long long mine = 0;
+// ---- GROUP BY key: hash or bitset + dense array (Section 5) -----------------
+// The union over j of the rows B(j) is a GROUP BY on the key k.  A row whose
+// possible outputs span at most kDenseSpan values, and which is predicted to
+// fill its span densely (at least one product per kDenseRatio values of the
+// span), unions its keys as bits and sums its values in a dense array; the
+// other rows sort (<= 256 products) or hash.  dense_mode 0: never dense, 1:
+// the density rule for rows the sort path does not take, 2: every row whose
+// span fits.
+constexpr uint32_t kDenseSpan = 4096;
+constexpr uint32_t kDenseRatio = 4;
+enum { ROW_SORT = 0, ROW_HASH = 1, ROW_DENSE = 2 };
+
+__global__ void k_spgemm_gcap(DTrie A, DTrie B, const uint32_t *ub, uint32_t n, uint32_t dense_mode, uint64_t *gcap,
+                              uint8_t *kind, uint32_t *kmin, unsigned long long *n_rows) {
+    unsigned long long mine = 0, dense = 0;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        uint64_t u = ub[p];
+        const uint64_t u = ub[p];
+        const uint32_t alo = __ldg(A.lv[0].offs + p), ahi = __ldg(A.lv[0].offs + p + 1);
+        const bool sortable = u <= kTab / 2 && ahi - alo <= 32;  // the sort path's rows (kEscPairs)
+        uint32_t kd = sortable ? ROW_SORT : ROW_HASH;
+        uint32_t lo_k = 0;
+        if (u > 0 && (dense_mode == 2 || (dense_mode == 1 && !sortable))) {
+            // span of the row's possible outputs: first and last k of every B(j)
+            uint32_t mn = 0xFFFFFFFFu, mx = 0;
+            for (uint32_t q = alo; q < ahi; ++q) {
+                uint32_t pj;
+                if (!lh_probe(B, 0, 0, 0, B.lv[0].n, __ldg(A.lv[1].vals + q), &pj)) continue;
+                const uint32_t b0 = __ldg(B.lv[0].offs + pj), b1 = __ldg(B.lv[0].offs + pj + 1);
+                if (b1 == b0) continue;
+                mn = min(mn, __ldg(B.lv[1].vals + b0));
+                mx = max(mx, __ldg(B.lv[1].vals + b1 - 1));
+            }
+            if (mx >= mn) {
+                const uint64_t span = (uint64_t)mx - mn + 1;
+                if (span <= kDenseSpan && (dense_mode == 2 || u * kDenseRatio >= span)) {
+                    kd = ROW_DENSE;
+                    lo_k = mn;
+                }
+            }
+        }
         uint64_t c = 0;
-        if (u > kTab / 2) {
+        if (kd == ROW_HASH && u > kTab / 2) {
             c = 64;
             while (c < 2 * u) c <<= 1;
         }
         gcap[p] = c;
-        mine += (u > kTab / 2 || aoffs[p + 1] - aoffs[p] > 32) ? 1ull : 0ull;
+        kind[p] = (uint8_t)kd;
+        kmin[p] = lo_k;
+        // rows for the hash kernel: the non-sortable ones, and with
+        // dense_mode 2 (no sort kernel) the sortable ones too
+        mine += (kd == ROW_HASH || (dense_mode == 2 && kd == ROW_SORT)) ? 1ull : 0ull;
+        dense += kd == ROW_DENSE ? 1ull : 0ull;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(LH_FULL, mine, o);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(n_hash_rows, mine);
+    for (int o = 16; o > 0; o >>= 1) {
+        mine += __shfl_xor_sync(LH_FULL, mine, o);
+        dense += __shfl_xor_sync(LH_FULL, dense, o);
+    }
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(n_rows, mine);
+    if ((threadIdx.x & 31) == 0 && dense) atomicAdd(n_rows + 2, dense);
+}
+
+constexpr int kDenseThreads = 256;
+
+struct DenseSmem {
+    double acc[kDenseSpan];
+    uint32_t bits[kDenseSpan / 32];
+    uint32_t wpre[kDenseSpan / 32];
+    uint32_t jb[kDenseThreads], jl[kDenseThreads], jp[kDenseThreads];
+    float ja[kDenseThreads];
+    uint32_t warp_tot[kDenseThreads / 32];
+};
+
+// inclusive block scan of one value per thread (256 threads)
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *warp_tot) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(LH_FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    uint32_t add = 0;
+    for (uint32_t w = 0; w < warp; ++w) add += warp_tot[w];
+    __syncthreads();
+    return x + add;
+}
+
+// One block per dense row: every product adds its exact fp64 value a * b to
+// its key's slot and sets the key's bit; the set bits, in ascending order,
+// then give the row's result already sorted (no sort, no hash).  The fp64
+// slots are the row's final per-key totals.
+__global__ void __launch_bounds__(kDenseThreads) k_spgemm_dense(
+    DTrie A, const float *av, DTrie B, const float *bv, uint32_t nA0, const uint8_t *kind, const uint32_t *kmin,
+    const uint64_t *tmp_off, uint32_t *tcol, float *tval, uint32_t *cnt) {
+    extern __shared__ __align__(16) unsigned char dn_raw[];
+    DenseSmem &S = *(DenseSmem *)dn_raw;
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t p = blockIdx.x; p < nA0; p += gridDim.x) {
+        if (kind[p] != ROW_DENSE) continue;
+        const uint32_t k0 = kmin[p];
+        for (uint32_t i = tid; i < kDenseSpan; i += kDenseThreads) S.acc[i] = 0.0;
+        for (uint32_t i = tid; i < kDenseSpan / 32; i += kDenseThreads) S.bits[i] = 0u;
+        __syncthreads();
+        const uint32_t alo = __ldg(A.lv[0].offs + p), ahi = __ldg(A.lv[0].offs + p + 1);
+        for (uint32_t q0 = alo; q0 < ahi; q0 += kDenseThreads) {
+            const uint32_t q = q0 + tid;
+            uint32_t bstart = 0, blen = 0;
+            float a = 0.f;
+            if (q < ahi) {
+                uint32_t pj;
+                if (lh_probe(B, 0, 0, 0, B.lv[0].n, __ldg(A.lv[1].vals + q), &pj)) {
+                    bstart = __ldg(B.lv[0].offs + pj);
+                    blen = __ldg(B.lv[0].offs + pj + 1) - bstart;
+                    a = __ldg(av + q);
+                }
+            }
+            const uint32_t incl = block_incl_scan(blen, S.warp_tot);
+            S.jb[tid] = bstart;
+            S.jl[tid] = blen;
+            S.jp[tid] = incl;
+            S.ja[tid] = a;
+            __syncthreads();
+            const uint32_t total = S.jp[kDenseThreads - 1];
+            for (uint32_t t = tid; t < total; t += kDenseThreads) {
+                uint32_t lo = 0, hi = kDenseThreads - 1;  // first staged entry with prefix > t
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (S.jp[mid] > t) hi = mid;
+                    else lo = mid + 1;
+                }
+                const uint32_t pos = S.jb[lo] + (t - (S.jp[lo] - S.jl[lo]));
+                const uint32_t d = __ldg(B.lv[1].vals + pos) - k0;
+                atomicAdd(&S.acc[d], (double)S.ja[lo] * (double)__ldg(bv + pos));   // exact product in fp64
+                atomicOr(&S.bits[d >> 5], 1u << (d & 31u));
+            }
+            __syncthreads();
+        }
+        // compaction in key order
+        const uint32_t w = tid;  // kDenseSpan / 32 == 128 words, one per thread below 128
+        const uint32_t c = w < kDenseSpan / 32 ? __popc(S.bits[w]) : 0u;
+        const uint32_t incl = block_incl_scan(c, S.warp_tot);
+        const uint64_t t0 = tmp_off[p];
+        if (w < kDenseSpan / 32) {
+            uint32_t bitsw = S.bits[w], o = incl - c;
+            while (bitsw) {
+                const uint32_t b = __ffs(bitsw) - 1;
+                bitsw &= bitsw - 1;
+                tcol[t0 + o] = k0 + 32 * w + b;
+                tval[t0 + o] = (float)S.acc[32 * w + b];
+                ++o;
+            }
+        }
+        if (tid == kDenseThreads - 1) cnt[p] = incl;
+        __syncthreads();
+    }
 }
 
 struct WarpSmem {
@@ -181,7 +323,7 @@ __device__ void warp_bitonic(uint32_t *key, float *val, uint32_t n, uint32_t npo
 __global__ void __launch_bounds__(kGemmThreads) k_spgemm_numeric(
     DTrie A, const float *av, DTrie B, const float *bv, uint32_t nA0, const uint64_t *tmp_off,
     const uint64_t *goff, uint32_t *gkey, float *ghi, float *glo, uint32_t *tcol, float *tval,
-    uint32_t *cnt) {
+    uint32_t *cnt, const uint8_t *kind, uint32_t take_sort_rows) {
     __shared__ WarpSmem sm_all[kGemmWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem &S = sm_all[warp];
@@ -190,8 +332,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm_numeric(
     for (uint32_t p = gw; p < nA0; p += nw) {
         const uint64_t cap64 = goff[p + 1] - goff[p];
         const bool global = cap64 > 0;
-        // rows with at most kEscPairs products and 32 A entries go to k_spgemm_esc
-        if (!global && __ldg(A.lv[0].offs + p + 1) - __ldg(A.lv[0].offs + p) <= 32) continue;
+        // dense rows have their own kernel; sortable rows go to k_spgemm_esc
+        // unless no sort kernel runs
+        const uint8_t kd = kind[p];
+        if (kd == ROW_DENSE || (kd == ROW_SORT && !take_sort_rows)) continue;
         const uint32_t cap = global ? (uint32_t)cap64 : kTab;
         uint32_t *key = global ? gkey + goff[p] : S.key;
         float *th = global ? ghi + goff[p] : S.hi;
@@ -609,7 +753,7 @@ lh_status lh_run_spmv(lh_ctx *ctx, const lh_trie *a, const float *x, uint64_t x_
     return LH_OK;
 }
 
-lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_result *r) {
+lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_result *r, uint32_t dense_mode) {
     if (a->nlevels != 2 || b->nlevels != 2 || a->nannos < 1 || b->nannos < 1 ||
         a->anno_type[0] != LH_T_F32 || b->anno_type[0] != LH_T_F32)
         return lh_fail(ctx, LH_EINVAL, "SpGEMM needs 2-level tries with f32 annotations");
@@ -618,10 +762,11 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
     r->nrows = n0;
     r->c_row = a->lv[0].vals;
     LH_TRY(res_alloc(ctx, r, &r->c_off, (size_t)n0 + 1));
-    uint32_t *ub = nullptr, *cnt = nullptr, *gkey = nullptr, *tcol = nullptr;
+    uint32_t *ub = nullptr, *cnt = nullptr, *gkey = nullptr, *tcol = nullptr, *kmin = nullptr;
+    uint8_t *kind = nullptr;
     uint64_t *tmp_off = nullptr, *gcap = nullptr, *goff = nullptr;
     unsigned long long *n_hash = nullptr;
-    unsigned long long hash_rows = 0;
+    unsigned long long hash_rows = 0, dense_rows = 0;
     float *ghi = nullptr, *glo = nullptr, *tval = nullptr;
     lh_status s = LH_OK;
     uint64_t U = 0, G = 0;
@@ -633,20 +778,24 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
     STEP(lh_alloc(ctx, &tmp_off, (size_t)n0 + 1));
     STEP(lh_alloc(ctx, &gcap, n0));
     STEP(lh_alloc(ctx, &goff, (size_t)n0 + 1));
-    STEP(lh_alloc(ctx, &n_hash, 2));
+    STEP(lh_alloc(ctx, &n_hash, 3));
+    STEP(lh_alloc(ctx, &kind, n0));
+    STEP(lh_alloc(ctx, &kmin, n0));
     if (s == LH_OK && n0) {
         LH_TRACED(ctx, "k_spgemm_bound", k_spgemm_bound<<<grid, T, 0, ctx->stream>>>(A, B, n0, ub));
-        cudaMemsetAsync(n_hash, 0, sizeof(unsigned long long), ctx->stream);
-        LH_TRACED(ctx, "k_spgemm_gcap", k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(ub, a->lv[0].offs, n0, gcap, n_hash));
+        cudaMemsetAsync(n_hash, 0, 3 * sizeof(unsigned long long), ctx->stream);
+        LH_TRACED(ctx, "k_spgemm_gcap", k_spgemm_gcap<<<grid, T, 0, ctx->stream>>>(A, B, ub, n0, dense_mode, gcap, kind,
+                                                                                 kmin, n_hash));
     }
     STEP(lh_scan_u32_to_u64(ctx, ub, tmp_off, n0));
     if (s == LH_OK && n0) {
         // U and the hash-row count in one readback
         LH_TRACED(ctx, "k_spgemm_sizes", k_spgemm_sizes<<<1, 32, 0, ctx->stream>>>(tmp_off + n0, n_hash));
-        uint64_t h[2] = {0, 0};
+        uint64_t h[3] = {0, 0, 0};
         STEP(lh_readback(ctx, n_hash, sizeof(h), h));
         U = h[0];
         hash_rows = h[1];
+        dense_rows = h[2];
     }
     if (s == LH_OK && hash_rows) {
         // global hash tables only for rows whose products overflow shared memory
@@ -669,7 +818,9 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_e, k_spgemm_esc<uint64_t>, kEscWarps * 32, 0);
         unsigned g3 = (unsigned)std::min<uint64_t>((n0 + kEscWarps - 1) / kEscWarps,
                                                    (uint64_t)ctx->num_sms * std::max(1, per_sm_e));
-        if (narrow)
+        if (dense_mode == 2) {
+            // no sort kernel: its rows are dense or hashed
+        } else if (narrow)
             LH_TRACED(ctx, "k_spgemm_esc", k_spgemm_esc<uint32_t><<<g3, kEscWarps * 32, 0, ctx->stream>>>(
                 A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ub, tmp_off, tcol, tval, cnt));
         else
@@ -677,7 +828,17 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
                 A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, ub, tmp_off, tcol, tval, cnt));
         if (hash_rows) LH_TRACED(ctx, "k_spgemm_numeric", k_spgemm_numeric<<<g2, kGemmThreads, 0, ctx->stream>>>(A, (const float *)a->anno[0], B,
                                                                (const float *)b->anno[0], n0, tmp_off,
-                                                               goff, gkey, ghi, glo, tcol, tval, cnt));
+                                                               goff, gkey, ghi, glo, tcol, tval, cnt, kind,
+                                                               dense_mode == 2 ? 1u : 0u));
+        if (dense_rows) {
+            const size_t smem = sizeof(DenseSmem);
+            cudaFuncSetAttribute(k_spgemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm_d = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_d, k_spgemm_dense, kDenseThreads, smem);
+            const unsigned g4 = (unsigned)std::min<uint64_t>(n0, (uint64_t)ctx->num_sms * std::max(1, per_sm_d));
+            LH_TRACED(ctx, "k_spgemm_dense", k_spgemm_dense<<<g4, kDenseThreads, smem, ctx->stream>>>(
+                A, (const float *)a->anno[0], B, (const float *)b->anno[0], n0, kind, kmin, tmp_off, tcol, tval, cnt));
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "spgemm: %s", cudaGetErrorString(e));
     }
@@ -691,7 +852,7 @@ lh_status lh_run_spgemm(lh_ctx *ctx, const lh_trie *a, const lh_trie *b, lh_resu
         LH_TRACED(ctx, "k_spgemm_gather", k_spgemm_gather<<<grid, T, 0, ctx->stream>>>(n0, tmp_off, r->c_off, tcol, tval, r->c_col, r->c_val));
 #undef STEP
     lh_free(ctx, ub); lh_free(ctx, cnt); lh_free(ctx, tmp_off); lh_free(ctx, gcap); lh_free(ctx, goff);
-    lh_free(ctx, n_hash);
+    lh_free(ctx, n_hash); lh_free(ctx, kind); lh_free(ctx, kmin);
     lh_free(ctx, tcol); lh_free(ctx, tval); lh_free(ctx, gkey); lh_free(ctx, ghi); lh_free(ctx, glo);
     if (s == LH_OK) {
         cudaError_t e = cudaGetLastError();

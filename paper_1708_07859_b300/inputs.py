@@ -231,6 +231,23 @@ def zipf_coo(nrows: int, ncols: int, per_row: int = 16, s: float = 1.1,
     return rows, cols, vals
 
 
+def banded_coo(nrows: int, ncols: int, per_row: int, width: int, seed: int):
+    """Sparse matrix whose row i holds ``per_row`` distinct columns drawn
+    uniformly from the band [i*ncols/nrows, i*ncols/nrows + width) (clipped
+    to the matrix); values fp32 U[-1, 1].  Products of banded matrices fill
+    narrow column ranges densely (the structured matrices of the paper's
+    sparse LA experiments)."""
+    rng = _rng(seed)
+    width = min(width, ncols)
+    starts = np.minimum((np.arange(nrows, dtype=np.int64) * ncols) // nrows, ncols - width)
+    # per_row distinct offsets in [0, width): the first per_row of a random ordering
+    offs = np.argsort(rng.random((nrows, width)), axis=1)[:, :per_row]
+    cols = (starts[:, None] + offs).reshape(-1)
+    rows = np.repeat(np.arange(nrows, dtype=np.int64), per_row)
+    vals = rng.uniform(-1.0, 1.0, size=rows.size).astype(np.float32)
+    return rows.astype(np.uint32), cols.astype(np.uint32), vals
+
+
 def uniform_coo(nrows: int, ncols: int, per_row: int, seed: int):
     """Small sparse matrix with ``per_row`` distinct uniform columns per row."""
     rng = _rng(seed)

@@ -781,12 +781,15 @@ def spmv_query(nrows, x, card_a):
                       semiring=SUMPROD_F32, group=[{"attr": 0, "card": nrows}], materialized=(0,))
 
 
-def spgemm_query(card_a, card_b):
-    """C(i,k) = sum_j A(i,j) B(j,k): A in slot 0 (i, j), B in slot 1 (j, k)."""
+def spgemm_query(card_a, card_b, group_impl=GROUP_AUTO):
+    """C(i,k) = sum_j A(i,j) B(j,k): A in slot 0 (i, j), B in slot 1 (j, k).
+    group_impl picks the GROUP BY key accumulator of the union over j
+    (Section 5): GROUP_DENSE the bitset + dense array wherever a row's span
+    fits, GROUP_PRIVATE sort / hash only, GROUP_AUTO the density rule."""
     return make_query(3, [{"slot": 0, "attrs": [0, 1], "anno": 0, "card": card_a},
                           {"slot": 1, "attrs": [1, 2], "anno": 0, "card": card_b}],
                       semiring=SUMPROD_F32, group=[{"attr": 0, "card": 1}, {"attr": 2, "card": 1}],
-                      materialized=(0, 2))
+                      materialized=(0, 2), group_impl=group_impl)
 
 
 def matrix_trie(ctx, rows, cols, vals, layout=None, dims=None):

@@ -54,9 +54,9 @@ def test_spmv_full_size(ctx, orc, lhlib):
     assert np.all(np.abs(y - w) <= TOL * wa + 1e-30)
 
 
-def spgemm(ctx, lh, A, B):
+def spgemm(ctx, lh, A, B, group_impl=0):
     ta, tb = build(ctx, lh, A), build(ctx, lh, B)
-    q = lh.spgemm_query(A[0].size, B[0].size)
+    q = lh.spgemm_query(A[0].size, B[0].size, group_impl)
     r = ctx.join_aggregate(q, lh.make_plan([0, 1, 2]), [ta, tb])
     v = r.wait()
     assert v.exec == lh.EXEC_SPGEMM
@@ -134,3 +134,37 @@ def test_spgemm_full_size_every_row(ctx, orc, lhlib):
     err = np.abs(vals.astype(np.float64) - wval)
     bad = err > TOL * wabs + 1e-30
     assert not bad.any(), (int(bad.sum()), float(np.max(err / np.maximum(wabs, 1e-30))))
+
+
+@pytest.mark.parametrize("impl", ["auto", "dense", "sort_hash"])
+def test_spgemm_group_by_key_implementations(ctx, orc, lhlib, impl):
+    """Section 5 GROUP BY key: banded matrices whose products fill narrow
+    column spans (dense rows: bitset + dense array under the density rule),
+    next to rows too wide for the dense array and sparse Zipf rows; every
+    implementation choice gives the oracle's C."""
+    lh = lhlib
+    gi = {"auto": lh.GROUP_AUTO, "dense": lh.GROUP_DENSE, "sort_hash": lh.GROUP_PRIVATE}[impl]
+    n = 3000
+    Ab = gen.banded_coo(n, n, 40, 200, 71)          # 40 entries per row: not a sort row
+    Bb = gen.banded_coo(n, n, 24, 300, 72)
+    Az = gen.uniform_coo(500, n, 6, 73)              # sparse rows over the whole range
+    A = (np.concatenate([Ab[0], Az[0] + n]), np.concatenate([Ab[1], Az[1]]), np.concatenate([Ab[2], Az[2]]))
+    nA = n + 500
+    rows, off, cols, vals = spgemm(ctx, lh, A, Bb, gi)
+    assert np.array_equal(rows, np.unique(A[0]))
+    woff, wcol, wval, wabs = orc.spgemm_rows(A, nA, Bb, n, n, rows)
+    assert np.array_equal(off.astype(np.uint64), woff) and np.array_equal(cols, wcol)
+    assert np.all(np.abs(vals - wval) <= TOL * wabs + 1e-30)
+
+
+def test_spgemm_dense_rows_wider_than_the_array(ctx, orc, lhlib):
+    """Forcing the dense accumulator: rows whose span exceeds it fall back to
+    the hash path, exactly."""
+    lh = lhlib
+    n = 20000
+    A = gen.banded_coo(n, n, 20, 6000, 74)
+    B = gen.banded_coo(n, n, 10, 3000, 75)
+    rows, off, cols, vals = spgemm(ctx, lh, A, B, lh.GROUP_DENSE)
+    woff, wcol, wval, wabs = orc.spgemm_rows(A, n, B, n, n, rows)
+    assert np.array_equal(off.astype(np.uint64), woff) and np.array_equal(cols, wcol)
+    assert np.all(np.abs(vals - wval) <= TOL * wabs + 1e-30)
