@@ -379,7 +379,16 @@ typedef struct {
  *     sums and uint64 counts added atomically.
  * The hash paths report their groups as key tuples (lh_result_view
  * group_keys); a shared table that fills up reports LH_EOVERFLOW at the
- * wait. */
+ * wait.
+ * Under LH_EXEC_SPGEMM the field picks how each row of C groups its
+ * products by output column (Section 5, the bitset + dense array against
+ * the hash table of Figure 5a): under AUTO rows of at most 256 products
+ * (and 32 entries of A) sort in registers, and a larger row takes a
+ * shared-memory bitset and dense fp64 array when its possible columns span
+ * at most 4096 values and its product bound fills at least a quarter of that
+ * span, else a hash table; DENSE takes the bitset and array for every row
+ * whose span fits; PRIVATE and SHARED never do.  The result (CSR, columns
+ * ascending) is the same under every choice. */
 typedef enum {
     LH_GROUP_AUTO = 0,
     LH_GROUP_DENSE = 1,
