@@ -399,7 +399,6 @@ __device__ __forceinline__ void stage_merge(const TileDesc &d, uint32_t *sa, uin
 // hold that value use the probe path instead (k_plan).
 
 constexpr uint32_t kSwz = kTile + 2 + (kTile + 2) / 32 + 2;
-constexpr uint32_t kBmWords = kTile;   // bitmap merge tiles: value span of at most kTile words
 __device__ __forceinline__ uint32_t swz(uint32_t i) { return i + (i >> 5); }
 
 // merge-path split on the padded slices (ties: A first)
@@ -465,55 +464,13 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
             __syncthreads();
             return;
         }
-        // A merge tile whose values span at most kBmWords words is counted
-        // as bitmaps: both slices set their bits in shared words (reusing
-        // the padded buffers), then the words are ANDed and popcounted.
-        // Each thread sets the bits of 16 consecutive elements of a slice,
-        // visiting them rotated by its lane so that a warp's loads and
-        // atomics fall on different banks and words.  The B slice's extra
-        // head element joins the bitmap, so a value common to both sets is
-        // counted in the tile holding its A element, exactly as the merge
-        // counts it.  Wider tiles take the padded copy and the merge.
-        bool bitmap = false;
-        uint32_t bm_words = 0;
         if (kind == K_MERGE) {
-            const uint32_t a_lo = la ? la_buf[offa] : 0xFFFFFFFFu, a_hi = la ? la_buf[offa + la - 1] : 0u;
-            const uint32_t b_lo = lbx ? lb_buf[offb] : 0xFFFFFFFFu, b_hi = lbx ? lb_buf[offb + lbx - 1] : 0u;
-            const uint32_t v_lo = min(a_lo, b_lo), v_hi = max(a_hi, b_hi);
-            const uint32_t base = v_lo & ~31u;
-            bm_words = v_hi >= v_lo ? ((v_hi - base) >> 5) + 1 : 0u;
-            bitmap = bm_words <= kBmWords;
-            if (bitmap) {
-                for (uint32_t w = threadIdx.x; w < bm_words; w += kThreads) {
-                    pa[w] = 0u;
-                    pb[w] = 0u;
-                }
-                __syncthreads();
-                const uint32_t rot = threadIdx.x & 15u;
-#pragma unroll 4
-                for (uint32_t k = 0; k < kItems; ++k) {
-                    const uint32_t i = threadIdx.x * kItems + ((k + rot) & 15u);
-                    if (i < la) {
-                        const uint32_t dv = la_buf[offa + i] - base;
-                        atomicOr(&pa[dv >> 5], 1u << (dv & 31u));
-                    }
-                    if (i < lbx) {
-                        const uint32_t dv = lb_buf[offb + i] - base;
-                        atomicOr(&pb[dv >> 5], 1u << (dv & 31u));
-                    }
-                }
-                if (threadIdx.x == 0 && lbx > (uint32_t)kTile) {  // the extra head past a full slice
-                    const uint32_t dv = lb_buf[offb + kTile] - base;
-                    atomicOr(&pb[dv >> 5], 1u << (dv & 31u));
-                }
-            } else {
-                // linear staging -> padded copy with sentinels
-                for (uint32_t k = threadIdx.x; k < la; k += kThreads) pa[swz(k)] = la_buf[offa + k];
-                for (uint32_t k = threadIdx.x; k < lbx; k += kThreads) pb[swz(k)] = lb_buf[offb + k];
-                if (threadIdx.x == 0) {
-                    pa[swz(la)] = 0xFFFFFFFFu;
-                    pb[swz(lbx)] = 0xFFFFFFFFu;
-                }
+            // linear staging -> padded copy with sentinels
+            for (uint32_t k = threadIdx.x; k < la; k += kThreads) pa[swz(k)] = la_buf[offa + k];
+            for (uint32_t k = threadIdx.x; k < lbx; k += kThreads) pb[swz(k)] = lb_buf[offb + k];
+            if (threadIdx.x == 0) {
+                pa[swz(la)] = 0xFFFFFFFFu;
+                pb[swz(lbx)] = 0xFFFFFFFFu;
             }
         }
         __syncthreads();
@@ -536,9 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
             }
         }
         uint32_t cnt = 0;
-        if (kind == K_MERGE && bitmap) {
-            for (uint32_t w = threadIdx.x; w < bm_words; w += kThreads) cnt += __popc(pa[w] & pb[w]);
-        } else if (kind == K_MERGE) {
+        if (kind == K_MERGE) {
             const uint32_t s = threadIdx.x * kItems;
             const uint32_t e = min(s + kItems, la + lb);
             if (s < e) {
