@@ -3,7 +3,8 @@
 // paper hands them to a BLAS GEMM).  Here: fp32 A (m x k) and B (k x n) are
 // split into bf16 high parts and bf16 residuals, the products run on the
 // 5th-generation tensor cores (tcgen05.mma, kind::f16, fp32 accumulators in
-// tensor memory), operands staged by TMA with the 128-byte swizzle, and one
+// tensor memory), operands staged by TMA with the 64-byte swizzle in a
+// four-deep ring of 32-wide k-blocks, and one
 // refinement step adds the residual cross products:
 //   C_bf16    = A_hi B_hi                       (fp32 output)
 //   C_refined = A_hi B_hi + (A_hi B_lo + A_lo B_hi)   (summed in fp64)
@@ -21,11 +22,14 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
-constexpr int kStages = 2;
+constexpr int BM = 128, BN = 256, BK = 32;
+constexpr int kStages = 4;
+// the public shape contract (k a multiple of 64) is kept independent of BK
+constexpr int kKMultiple = 64;
+static_assert(kKMultiple % BK == 0, "k contract must cover whole k-blocks");
 constexpr int kThreads = 128;
-constexpr uint32_t kATile = BM * BK * 2;                   // 16 KB
-constexpr uint32_t kBTile = BN * BK * 2;                   // 32 KB
+constexpr uint32_t kATile = BM * BK * 2;                   // 8 KB
+constexpr uint32_t kBTile = BN * BK * 2;                   // 16 KB
 constexpr uint32_t kStageBytes = 2 * kATile + 2 * kBTile;  // A_hi, A_lo, B_hi, B_lo
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
@@ -109,15 +113,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// K-major operand tile in the 128-byte-swizzle layout TMA writes: rows of
-// 128 bytes, 8-row groups 1024 bytes apart (SBO), swizzle mode 2, version 1.
+// K-major operand tile in the 64-byte-swizzle layout TMA writes: rows of
+// 64 bytes (one 32-wide k-block), 8-row groups 512 bytes apart (SBO), swizzle
+// mode 4, version 1.  The k-th 16-wide MMA slice starts 32 k bytes into the row.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;             // leading byte offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset: 8 rows of 64 bytes
     d |= (uint64_t)1 << 46;             // descriptor version
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    d |= (uint64_t)4 << 61;             // 64-byte swizzle
     return d;
 }
 
@@ -358,7 +363,7 @@ lh_status get_encoder(lh_ctx *ctx, EncodeTiledFn *fn) {
     return LH_OK;
 }
 
-// rows x cols bf16 row-major, box (64 columns, box_rows rows), 128-byte swizzle
+// rows x cols bf16 row-major, box (BK columns, box_rows rows), 64-byte swizzle
 lh_status make_map(lh_ctx *ctx, EncodeTiledFn enc, CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols,
                    uint32_t box_rows) {
     cuuint64_t dims[2] = {cols, rows};
@@ -366,7 +371,7 @@ lh_status make_map(lh_ctx *ctx, EncodeTiledFn enc, CUtensorMap *map, const void 
     cuuint32_t box[2] = {BK, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return lh_fail(ctx, LH_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return LH_OK;
@@ -378,7 +383,7 @@ extern "C" lh_status lh_dense_matmul(lh_ctx *ctx, const float *A, const float *B
                                      double *c_refined) {
     if (!ctx) return LH_EINVAL;
     if (!A || !B || !c_bf16) return lh_fail(ctx, LH_EINVAL, "null argument");
-    if (m <= 0 || n <= 0 || k <= 0 || m % BM || n % BN || k % BK)
+    if (m <= 0 || n <= 0 || k <= 0 || m % BM || n % BN || k % kKMultiple)
         return lh_fail(ctx, LH_EUNSUPPORTED, "dense block needs m %% 128 == 0, n %% 256 == 0, k %% 64 == 0 (got %d, %d, %d)",
                        m, n, k);
     if ((uintptr_t)c_bf16 % 16 || (c_refined && (uintptr_t)c_refined % 16))

@@ -15,6 +15,8 @@
 //      (bitset: one word and a rank; uint: binary search) -- the k-way
 //      intersection; survivors become the next frontier (warp-aggregated
 //      compaction), or at the last attribute are counted / aggregated.
+// At the root (depth 0) the sets are level-0 sets whose sizes the host
+// already knows, so step 1 and the scan are skipped there.
 // The candidate space is cut into chunks of at most `cap` candidates, so the
 // frontier memory is bounded whatever the output size; each chunk recurses
 // before the next is expanded (depth-first over chunks).
@@ -185,8 +187,117 @@ __device__ __forceinline__ uint32_t find_entry(const uint64_t *off, uint32_t nF,
 // there (a few shared loads instead of a search over the whole frontier).
 constexpr uint32_t kWin = 256;
 
+// ---- count-only intersection of two sets at the last attribute ------------
+// A COUNT join without GROUP BY needs only |S ∩ T| at its last attribute.
+// Frontier entries whose smaller set holds at least kWarpMinSet elements are
+// taken off the per-candidate path and counted by warps, in work items of at
+// most kSegWork elements, so a hub entry is spread over many warps:
+//   MERGE   both sets uint, |T| <= kMergeRatio |S|: merge path.  Item g covers
+//           diagonals [g kSegWork, (g+1) kSegWork) of the merge of S and T;
+//           the warp steps through it with a 32-element window of each set,
+//           finds every S element's lower bound in T's window with five
+//           shuffles, counts the equal ones below the windows' common bound
+//           with a ballot, and advances each window past that bound.
+//   SCAN_S  T a bitset, or T much larger than S: lanes take S's elements,
+//           each probes T (bitset word, or a binary search whose lower end
+//           moves forward with the warp's previous element -- S is sorted).
+//   SCAN_T  S a bitset and T uint of comparable size: lanes take T's
+//           elements and probe S's bitset.
+constexpr uint32_t kWarpMinSet = 32;
+constexpr uint32_t kSegWork = 2048;
+constexpr uint32_t kMergeRatio = 8;
+constexpr unsigned long long kNoItem = ~0ull;
+enum { K_MERGE = 0, K_SCAN_S = 1, K_SCAN_T = 2 };
+
+struct LastPair {
+    uint32_t pS, pT;            // positions (in the depth's relation list) of the smaller and the other set
+    uint32_t sLo, sHi, tLo, tHi, sSet, tSet;
+    uint32_t kind;
+    uint64_t work, nseg;
+};
+
+// The two sets of frontier entry i at the last depth (both relations stored
+// as tries), the smaller one first on ties as k_sizes picks its driver.
+__device__ __forceinline__ void pair_side(const JQuery &q, const JDepth &D, const uint32_t *posF, uint32_t capF,
+                                          uint32_t i, uint32_t p, uint32_t &lo, uint32_t &hi, uint32_t &set,
+                                          bool &bs) {
+    const JEdge &E = q.E[D.e[p]];
+    const uint32_t L = D.lvl[p];
+    const uint32_t parent = L ? posF[(uint64_t)D.e[p] * capF + i] : 0u;
+    lh_set_range(E.t, L, parent, lo, hi);
+    set = L ? parent : 0u;
+    const DLevel &lv = E.t.lv[L];
+    bs = lv.bs_slot != nullptr && __ldg(lv.bs_slot + set) != LH_NOSLOT;
+}
+
+__device__ __forceinline__ void last_pair(const JQuery &q, const JDepth &D, const uint32_t *posF, uint32_t capF,
+                                          uint32_t i, LastPair &P) {
+    uint32_t lo0, hi0, set0, lo1, hi1, set1;
+    bool bs0, bs1;
+    pair_side(q, D, posF, capF, i, 0, lo0, hi0, set0, bs0);
+    pair_side(q, D, posF, capF, i, 1, lo1, hi1, set1, bs1);
+    const bool swap = hi1 - lo1 < hi0 - lo0;
+    P.pS = swap ? 1u : 0u;
+    P.pT = swap ? 0u : 1u;
+    P.sLo = swap ? lo1 : lo0; P.sHi = swap ? hi1 : hi0; P.sSet = swap ? set1 : set0;
+    P.tLo = swap ? lo0 : lo1; P.tHi = swap ? hi0 : hi1; P.tSet = swap ? set0 : set1;
+    const bool bsS = swap ? bs1 : bs0, bsT = swap ? bs0 : bs1;
+    const uint64_t sn = P.sHi - P.sLo, tn = P.tHi - P.tLo;
+    const bool close = tn <= (uint64_t)kMergeRatio * sn;
+    if (bsT) P.kind = K_SCAN_S;
+    else if (!bsS) P.kind = close ? K_MERGE : K_SCAN_S;
+    else P.kind = close ? K_SCAN_T : K_SCAN_S;
+    P.work = P.kind == K_MERGE ? sn + tn : P.kind == K_SCAN_S ? sn : tn;
+    P.nseg = (P.work + kSegWork - 1) / kSegWork;
+}
+
+// Merge-path split: the number of A elements among the first `diag`
+// elements of the merge of sorted A (s) and B (t), A first on equal values.
+__device__ __forceinline__ uint32_t merge_split(const uint32_t *A, uint32_t s, const uint32_t *B, uint32_t t,
+                                                uint64_t diag) {
+    uint32_t lo = diag > t ? (uint32_t)(diag - t) : 0u;
+    uint32_t hi = (uint32_t)(diag < s ? diag : (uint64_t)s);
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(A + mid) <= __ldg(B + (diag - mid - 1))) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// |A[a0, a1) ∩ B[b0, b1)| by one warp (all lanes, uniform bounds).  Every
+// round loads a window of up to 32 elements of each; m, the smaller of the
+// windows' last elements, bounds what this round settles: an A element <= m
+// has its match, if any, inside B's window, and B elements <= m can match no
+// later A element.  At least one window is used up per round.
+__device__ __forceinline__ uint32_t warp_merge_count(const uint32_t *A, uint32_t a0, uint32_t a1, const uint32_t *B,
+                                                     uint32_t b0, uint32_t b1, uint32_t lane) {
+    uint32_t cnt = 0;
+    while (a0 < a1 && b0 < b1) {
+        const uint32_t na = min(32u, a1 - a0), nb = min(32u, b1 - b0);
+        const bool va = lane < na, vb = lane < nb;
+        const uint32_t a = va ? __ldg(A + a0 + lane) : 0xFFFFFFFFu;
+        const uint32_t b = vb ? __ldg(B + b0 + lane) : 0xFFFFFFFFu;
+        const uint32_t m = min(__shfl_sync(LH_FULL, a, na - 1), __shfl_sync(LH_FULL, b, nb - 1));
+        // lower bound of a among B's window (lanes past nb hold the maximum)
+        uint32_t pos = 0;
+#pragma unroll
+        for (uint32_t st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(LH_FULL, b, pos + st - 1) < a) pos += st;
+        // every lane takes part in the shuffle (pos < 32 always); only then
+        // is the result filtered
+        const uint32_t bp = __shfl_sync(LH_FULL, b, pos);
+        const bool hit = va && pos < nb && bp == a && a <= m;
+        cnt += __popc(__ballot_sync(LH_FULL, hit));
+        a0 += __popc(__ballot_sync(LH_FULL, va && a <= m));
+        b0 += __popc(__ballot_sync(LH_FULL, vb && b <= m));
+    }
+    return cnt;
+}
+
 __global__ void k_sizes(JQuery q, uint32_t d, const uint32_t *posF, uint32_t nF, uint32_t capF,
-                        uint32_t *size, uint8_t *drv, unsigned long long *elems) {
+                        uint32_t *size, uint8_t *drv, unsigned long long *elems, uint64_t *items,
+                        unsigned long long *n_items, uint64_t cap_items) {
     const JDepth &D = q.D[d];
     uint64_t local = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
@@ -207,12 +318,101 @@ __global__ void k_sizes(JQuery q, uint32_t d, const uint32_t *posF, uint32_t nF,
             if (sz < best) { best = sz; bi = p; }
         }
         if (bi == 0xFF) { best = flat_n; bi = flat_p; }
+        if (items != nullptr && best >= kWarpMinSet) {
+            // a large pair of sets at the last COUNT attribute: its work
+            // items go to k_count_pairs, and it drives no candidates here.
+            // When the item list is full the entry stays on this path (the
+            // slots it reserved below the capacity are marked empty).
+            LastPair P;
+            last_pair(q, D, posF, capF, i, P);
+            const unsigned long long at = atomicAdd(n_items, (unsigned long long)P.nseg);
+            if (at + P.nseg <= cap_items) {
+                for (uint64_t g = 0; g < P.nseg; ++g) items[at + g] = ((uint64_t)i << 24) | g;
+                best = 0;
+            } else {
+                for (uint64_t g = at; g < cap_items && g < at + P.nseg; ++g) items[g] = kNoItem;
+            }
+        }
         size[i] = best;
         drv[i] = (uint8_t)bi;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(LH_FULL, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(elems, (unsigned long long)local);
+}
+
+// Work items of the large last-attribute pairs (see kWarpMinSet): one warp
+// per item, grid-strided; item = entry << 24 | segment.
+__global__ void __launch_bounds__(kThreads) k_count_pairs(JQuery q, uint32_t d, const uint32_t *posF, uint32_t capF,
+                                                          const uint64_t *items, uint64_t n_items,
+                                                          unsigned long long *count, unsigned long long *visited) {
+    const JDepth &D = q.D[d];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long cnt = 0, vis = 0;
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_items; w += nw) {
+        const uint64_t it = __ldg((const unsigned long long *)items + w);
+        if (it == kNoItem) continue;
+        const uint32_t i = (uint32_t)(it >> 24);
+        const uint64_t g = it & 0xFFFFFFull;
+        LastPair P;
+        last_pair(q, D, posF, capF, i, P);
+        const JEdge &ES = q.E[D.e[P.pS]];
+        const JEdge &ET = q.E[D.e[P.pT]];
+        const uint32_t LS = D.lvl[P.pS], LT = D.lvl[P.pT];
+        const uint32_t *S = ES.t.lv[LS].vals + P.sLo;
+        const uint32_t *T = ET.t.lv[LT].vals + P.tLo;
+        const uint32_t sn = P.sHi - P.sLo, tn = P.tHi - P.tLo;
+        const uint64_t w0 = g * kSegWork, w1 = (w0 + kSegWork < P.work) ? w0 + kSegWork : P.work;
+        if (P.kind == K_MERGE) {
+            const uint32_t ia0 = merge_split(S, sn, T, tn, w0), ia1 = merge_split(S, sn, T, tn, w1);
+            const uint32_t ib0 = (uint32_t)(w0 - ia0), ib1 = (uint32_t)(w1 - ia1);
+            // S elements of this item; a match of the last one may be T[ib1]
+            const uint32_t bend = min(ib1 + 1, tn);
+            cnt += warp_merge_count(S, ia0, ia1, T, ib0, bend, lane);
+            vis += (ia1 - ia0) + (bend - ib0);
+        } else {
+            // lanes take the elements [w0, w1) of the scanned set X and probe
+            // the other set Y
+            const bool scan_s = P.kind == K_SCAN_S;
+            const uint32_t *X = scan_s ? S : T;
+            const JEdge &EY = scan_s ? ET : ES;
+            const uint32_t LY = scan_s ? LT : LS;
+            const uint32_t ylo = scan_s ? P.tLo : P.sLo, yhi = scan_s ? P.tHi : P.sHi;
+            const uint32_t yset = scan_s ? P.tSet : P.sSet;
+            const DLevel &ly = EY.t.lv[LY];
+            const bool ybs = ly.bs_slot != nullptr && __ldg(ly.bs_slot + yset) != LH_NOSLOT;
+            uint32_t lb = ylo;   // lower end of the uint search: the warp's previous elements are smaller
+            for (uint64_t k = w0; k < w1; k += 32) {
+                const uint32_t nv = (w1 - k < 32) ? (uint32_t)(w1 - k) : 32u;
+                const bool v = lane < nv;
+                const uint32_t x = v ? __ldg(X + k + lane) : 0u;
+                bool hit = false;
+                if (ybs) {
+                    uint32_t pos;
+                    hit = v && lh_probe(EY.t, LY, yset, ylo, yhi, x, &pos);
+                } else {
+                    const uint32_t p = v ? lh_lower_bound(ly.vals, lb, yhi, x) : yhi;
+                    hit = v && p < yhi && __ldg(ly.vals + p) == x;
+                    lb = __shfl_sync(LH_FULL, p, nv - 1);
+                }
+                cnt += __popc(__ballot_sync(LH_FULL, hit));
+            }
+            vis += 2 * (w1 - w0);
+        }
+    }
+    if (lane == 0 && cnt) atomicAdd(count, cnt);
+    if (lane == 0 && vis) atomicAdd(visited, vis);
+}
+
+// The root frontier entry (depth 0) as k_sizes and the scan would leave it.
+__global__ void k_root(uint32_t *size, uint8_t *drv, uint64_t *off, uint32_t best, uint32_t bi,
+                       unsigned long long el, unsigned long long *elems) {
+    size[0] = best;
+    drv[0] = (uint8_t)bi;
+    off[0] = 0;
+    off[1] = best;
+    if (el) atomicAdd(elems, el);
 }
 
 struct ExpandOut {
@@ -507,6 +707,8 @@ struct Driver {
     uint32_t n_keygroups;
     uint32_t mode_last;   // M_COUNT or M_AGG
     bool shortcut_last;   // last depth has one set and nothing to aggregate: add sizes
+    bool pairs_last;      // last depth counts two trie sets: large pairs go to k_count_pairs
+    unsigned grid_pairs;
     size_t smem_bytes;
     unsigned grid_expand;
     std::chrono::steady_clock::time_point t0;
@@ -525,21 +727,63 @@ struct Driver {
         uint32_t *size = nullptr;
         uint8_t *drvb = nullptr;
         uint64_t *off = nullptr;
+        const bool last = d + 1 == q.nd;
+        const bool pairs = last && pairs_last;
+        uint64_t *items = nullptr;
+        const uint64_t cap_items = pairs ? (uint64_t)nF + (1u << 18) : 0;
+        // off[nF]: the candidate total; off[nF + 1]: the pair work items
         lh_status s = lh_alloc(ctx, &size, nF);
         if (s == LH_OK) s = lh_alloc(ctx, &drvb, nF);
-        if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)nF + 1);
-        uint64_t total = 0;
+        if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)nF + 2);
+        if (s == LH_OK && pairs) s = lh_alloc(ctx, &items, cap_items);
+        uint64_t rb[2] = {0, 0};
         if (s == LH_OK) {
+            if (pairs && cudaMemsetAsync(off + nF + 1, 0, sizeof(uint64_t), ctx->stream) != cudaSuccess)
+                s = lh_fail(ctx, LH_ECUDA, "memset failed");
+        }
+        const bool root = d == 0 && posF == nullptr && !last;
+        if (s == LH_OK && root) {
+            // the root's sets are the level-0 sets, whose sizes the host
+            // knows: the driver is picked here, with no sizes kernel, scan
+            // or readback
+            const JDepth &D = q.D[0];
+            uint32_t best = 0xFFFFFFFFu, bi = 0xFF, flat_n = 0xFFFFFFFFu, flat_p = 0xFF;
+            unsigned long long el = 0;
+            for (uint32_t p = 0; p < D.np; ++p) {
+                const JEdge &E = q.E[D.e[p]];
+                if (E.is_flat) {
+                    if (E.flat_n < flat_n) { flat_n = E.flat_n; flat_p = p; }
+                    continue;
+                }
+                const uint32_t sz = E.t.lv[0].n;
+                el += sz;
+                if (sz < best) { best = sz; bi = p; }
+            }
+            if (bi == 0xFF) { best = flat_n; bi = flat_p; }
+            LH_TRACED(ctx, "k_root", k_root<<<1, 1, 0, ctx->stream>>>(size, drvb, off, best, bi, el,
+                                                                       (unsigned long long *)r->d_elems));
+            rb[0] = best;
+        } else if (s == LH_OK) {
             unsigned g = (unsigned)std::min<uint64_t>(lh_blocks(nF, kThreads), (uint64_t)ctx->num_sms * 8);
             LH_TRACED(ctx, "k_sizes", k_sizes<<<g, kThreads, 0, ctx->stream>>>(q, d, posF, nF, capF, size, drvb,
-                                                     (unsigned long long *)r->d_elems));
+                                                     (unsigned long long *)r->d_elems, items,
+                                                     (unsigned long long *)(off + nF + 1), cap_items));
             s = lh_scan_u32_to_u64(ctx, size, off, nF);
+            if (s == LH_OK) s = lh_readback(ctx, off + nF, (pairs ? 2 : 1) * sizeof(uint64_t), rb);
         }
-        if (s == LH_OK) s = lh_readback(ctx, off + nF, sizeof(uint64_t), &total);
-        const bool last = d + 1 == q.nd;
+        const uint64_t total = rb[0], n_items = std::min<uint64_t>(rb[1], cap_items);
         if (s == LH_OK && !(last && shortcut_last)) r->visited += total * q.D[d].np;
         if (s == LH_OK && last) {
-            if (shortcut_last) {
+            if (n_items) {
+                const unsigned g = (unsigned)std::min<uint64_t>(lh_blocks(n_items * 32, kThreads), grid_pairs);
+                LH_TRACED(ctx, "k_count_pairs", k_count_pairs<<<g, kThreads, 0, ctx->stream>>>(
+                                                    q, d, posF, capF, items, n_items, (unsigned long long *)r->d_count,
+                                                    (unsigned long long *)r->d_elems + 1));
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "count pairs: %s", cudaGetErrorString(e));
+            }
+            if (s != LH_OK) {
+            } else if (shortcut_last) {
                 r->host_count += total;
             } else if (total) {
                 ExpandOut o = {};
@@ -598,6 +842,7 @@ struct Driver {
         lh_free(ctx, size);
         lh_free(ctx, drvb);
         lh_free(ctx, off);
+        lh_free(ctx, items);
         return s;
     }
 };
@@ -783,6 +1028,13 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
     for (uint32_t p = 0; p < DL.np; ++p) nonflat += jq.E[DL.e[p]].is_flat ? 0 : 1;
     dr.mode_last = (is_count && q->n_group == 0) ? M_COUNT : M_AGG;
     dr.shortcut_last = dr.mode_last == M_COUNT && DL.np == 1 && nonflat == 1;
+    if (q->isect_impl > LH_ISECT_PROBE) return lh_fail(ctx, LH_EINVAL, "unknown isect_impl %u", q->isect_impl);
+    dr.pairs_last = dr.mode_last == M_COUNT && DL.np == 2 && nonflat == 2 && q->isect_impl == LH_ISECT_AUTO;
+    {
+        int pp = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pp, k_count_pairs, kThreads, 0);
+        dr.grid_pairs = (unsigned)(ctx->num_sms * std::max(1, pp));
+    }
     dr.cap = 1u << 22;
     dr.smem_bytes = 0;
     int per_sm = 4;
@@ -803,9 +1055,9 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
     // results
     r->ngroups = (dr.mode_last == M_AGG && jq.gmode == G_DENSE) ? jq.ngroups : 0;
     LH_TRY(res_alloc(ctx, r, &r->d_count, 1));
-    LH_TRY(res_alloc(ctx, r, &r->d_elems, 1));
+    LH_TRY(res_alloc(ctx, r, &r->d_elems, 2));   // [0] elements, [1] elements read by k_count_pairs
     LH_CU(cudaMemsetAsync(r->d_count, 0, sizeof(uint64_t), ctx->stream));
-    LH_CU(cudaMemsetAsync(r->d_elems, 0, sizeof(uint64_t), ctx->stream));
+    LH_CU(cudaMemsetAsync(r->d_elems, 0, 2 * sizeof(uint64_t), ctx->stream));
     if (r->ngroups) {
         LH_TRY(res_alloc(ctx, r, &r->d_gsum, r->ngroups));
         LH_TRY(res_alloc(ctx, r, &r->d_gcount, r->ngroups));
@@ -947,11 +1199,11 @@ extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v
         if (s != LH_OK) return s;
         r->ngroups = (uint32_t)G;
     }
-    uint64_t cnt = 0, el = 0;
+    uint64_t cnt = 0, el[2] = {0, 0};
     if (r->d_count) LH_CU(cudaMemcpy(&cnt, r->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
-    if (r->d_elems) LH_CU(cudaMemcpy(&el, r->d_elems, sizeof(el), cudaMemcpyDeviceToHost));
-    v->elements = el;
-    v->visited = r->visited;
+    if (r->d_elems) LH_CU(cudaMemcpy(el, r->d_elems, sizeof(el), cudaMemcpyDeviceToHost));
+    v->elements = el[0];
+    v->visited = r->visited + el[1];
     v->count = cnt + r->host_count;
     if (r->ngroups) {
         std::vector<double> gs(r->ngroups);

@@ -20,6 +20,9 @@ def check_bitsets(tr, lv_index, arrays, words, rank):
     prev = arrays[lv_index - 1] if lv_index > 0 else None
     nsets = 1 if lv_index == 0 else prev["vals"].size
     checked = 0
+    # arena-wide rank: bits of all earlier words (popcounts from the bytes)
+    all_pc = np.unpackbits(np.ascontiguousarray(words).view(np.uint8)).reshape(-1, 32).sum(axis=1).astype(np.int64)
+    prefix = np.concatenate([[0], np.cumsum(all_pc)[:-1]])
     for s in range(nsets):
         slot = lv["bs_slot"][s]
         if slot == 0xFFFFFFFF:
@@ -31,9 +34,7 @@ def check_bitsets(tr, lv_index, arrays, words, rank):
         ws = words[w0:w0 + nw]
         bits = np.unpackbits(ws.view(np.uint8), bitorder="little").astype(bool)
         assert np.array_equal(np.flatnonzero(bits) + base, elems)
-        # arena-wide rank: bits of all earlier words; rank base = rank of the first word
-        all_pc = np.array([bin(int(x)).count("1") for x in words[:w0 + nw]], dtype=np.int64)
-        prefix = np.concatenate([[0], np.cumsum(all_pc)[:-1]])
+        # rank base = rank of the set's first word
         assert rbase == prefix[w0]
         assert np.array_equal(rank[w0:w0 + nw].astype(np.int64), prefix[w0:w0 + nw])
         checked += 1
