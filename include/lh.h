@@ -359,7 +359,24 @@ typedef struct {
     uint64_t group_capacity;    /* hash GROUP BY: slots of the shared table (0 = twice the product of the
                                    columns' domains -- declared cards, else the distinct values their
                                    relations can hold -- clamped to [2^12, 2^24]) */
+    uint32_t isect_impl;        /* lh_isect_impl */
 } lh_query;
+
+/* How the generic driver intersects at the last attribute of a COUNT query
+ * without GROUP BY when that attribute joins exactly two stored relations
+ * (Algorithm 1's innermost intersection, of which only the size is used).
+ *   LH_ISECT_AUTO: frontier entries whose smaller set holds at least 32
+ *     elements are counted by warps in work items of at most 2048 elements
+ *     (a hub's pair spreads over many warps): merge path when both sets are
+ *     uint and within 8x of each other in size (windows of 32 elements of
+ *     each, matches found with shuffles and counted with a ballot); else the
+ *     elements of one set are probed in the other (a bitset word, or a
+ *     binary search whose lower end advances with the sorted probes).
+ *     Smaller entries take the LH_ISECT_PROBE path.
+ *   LH_ISECT_PROBE: one thread per element of the smaller set, probed in the
+ *     other (the path of every other attribute).
+ * Both give the same count. */
+typedef enum { LH_ISECT_AUTO = 0, LH_ISECT_PROBE = 1 } lh_isect_impl;
 
 /* How a GROUP BY on annotations (or keys) accumulates (Section 5).
  *   LH_GROUP_AUTO: dense per-group arrays when at most two columns all

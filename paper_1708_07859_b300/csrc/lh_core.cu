@@ -355,7 +355,10 @@ lh_status scan_impl(lh_ctx *ctx, const TI *in, TO *out, uint64_t n) {
     }
     TO *sums = nullptr, *pref = nullptr;
     LH_TRY(lh_alloc(ctx, &sums, tiles));
-    LH_TRY(lh_alloc(ctx, &pref, tiles + 1));
+    if (lh_status s0 = lh_alloc(ctx, &pref, tiles + 1); s0 != LH_OK) {
+        lh_free(ctx, sums);
+        return s0;
+    }
     LH_TRACED(ctx, "k_tile_sums", k_tile_sums<TI, TO><<<(unsigned)tiles, kScanThreads, 0, ctx->stream>>>(in, n, sums));
     LH_LAUNCH_CHECK();
     lh_status s = scan_impl<TO, TO>(ctx, sums, pref, tiles);

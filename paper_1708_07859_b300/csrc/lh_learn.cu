@@ -153,6 +153,7 @@ unsigned blocks_for(uint64_t n) { return (unsigned)((n + 255) / 256); }
 
 lh_status ensure_cap(lh_ctx *ctx, lh_model *m, uint32_t n) {
     if (n <= m->cap) return LH_OK;
+    m->cap = 0;   // until every buffer is reallocated: a failure here leaves none usable
     float **bufs[] = {&m->z1, &m->z2, &m->dz1, &m->dz2};
     for (float **b : bufs) {
         lh_free(ctx, *b);

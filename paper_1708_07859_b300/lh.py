@@ -24,6 +24,7 @@ MAX_ANNOS = 4
 NFEAT = 64
 MAX_GROUP = 6
 GROUP_AUTO, GROUP_DENSE, GROUP_PRIVATE, GROUP_SHARED = 0, 1, 2, 3
+ISECT_AUTO, ISECT_PROBE = 0, 1
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EOVERFLOW = range(7)
 COUNT_U64, SUM_F32_KAHAN, SUM_F64, SUMPROD_F32 = range(4)
@@ -109,7 +110,8 @@ class Query(C.Structure):
     _fields_ = [("n_attrs", C.c_uint32), ("n_edges", C.c_uint32), ("edges", Edge * MAX_EDGES),
                 ("semiring", C.c_uint32), ("n_group", C.c_uint32), ("group", Group * MAX_GROUP),
                 ("materialized_mask", C.c_uint32), ("eq_selected_mask", C.c_uint32),
-                ("exec", C.c_uint32), ("group_impl", C.c_uint32), ("group_capacity", C.c_uint64)]
+                ("exec", C.c_uint32), ("group_impl", C.c_uint32), ("group_capacity", C.c_uint64),
+                ("isect_impl", C.c_uint32)]
 
 
 class Plan(C.Structure):
@@ -274,7 +276,8 @@ def torch_allocator_fns():
 class Context:
     """An lh_ctx bound to the current torch CUDA stream (or ``stream``).
     allocator="torch" takes every device allocation from torch's caching
-    allocator (lh_create_with_allocator) instead of the context's own pool."""
+    allocator (lh_create_with_allocator) instead of the context's own pool;
+    an AllocFns gives the callbacks directly."""
 
     def __init__(self, stream=None, allocator=None):
         torch = _torch()
@@ -286,9 +289,12 @@ class Context:
         if allocator is None:
             self._check(lib().lh_create(C.byref(self.h), C.c_void_p(s.cuda_stream)))
         else:
-            if allocator != "torch":
-                raise ValueError("allocator: None or 'torch'")
-            self._fns = torch_allocator_fns()   # kept alive with the context
+            if isinstance(allocator, AllocFns):
+                self._fns = allocator               # the caller keeps the callbacks alive too
+            elif allocator == "torch":
+                self._fns = torch_allocator_fns()   # kept alive with the context
+            else:
+                raise ValueError("allocator: None, 'torch' or an AllocFns")
             self._check(lib().lh_create_with_allocator(C.byref(self.h), C.c_void_p(s.cuda_stream),
                                                        C.byref(self._fns)))
 
@@ -556,7 +562,7 @@ class Result:
 # ----------------------------------------------------------------- queries
 
 def make_query(n_attrs, edges, semiring=COUNT_U64, group=(), materialized=(), eq_selected=(),
-               exec_hint=EXEC_AUTO, group_impl=0, group_capacity=0):
+               exec_hint=EXEC_AUTO, group_impl=0, group_capacity=0, isect_impl=0):
     """edges: list of dicts {slot, attrs, anno=-1, flat=None (tensor), card=0};
     group: list of dicts {edge, anno=-1, attr=0, card}."""
     q = Query()
@@ -587,6 +593,7 @@ def make_query(n_attrs, edges, semiring=COUNT_U64, group=(), materialized=(), eq
     q.exec = exec_hint
     q.group_impl = group_impl
     q.group_capacity = group_capacity
+    q.isect_impl = isect_impl
     return q
 
 
@@ -627,7 +634,7 @@ class GraphJoin:
     dst): each pattern edge is a hyperedge on E.  Tries of E are built in the
     key orders the plan needs (forward (src, dst) and reverse (dst, src))."""
 
-    def __init__(self, ctx, src_dev, dst_dev, shape, layout=(32, 32), card=None):
+    def __init__(self, ctx, src_dev, dst_dev, shape, layout=(32, 32), card=None, isect_impl=ISECT_AUTO):
         self.ctx = ctx
         self.src, self.dst = src_dev, dst_dev
         self.n_attrs, self.pattern = GRAPH_SHAPES[shape]
@@ -635,7 +642,7 @@ class GraphJoin:
         self.tries = {}
         card = int(src_dev.numel()) if card is None else int(card)
         self.query = make_query(self.n_attrs, [{"slot": 0, "attrs": list(p), "card": card}
-                                               for p in self.pattern])
+                                               for p in self.pattern], isect_impl=isect_impl)
 
     def rel(self):
         """lh_relation_desc of E(src, dst) (for the learned / exhaustive planners)."""

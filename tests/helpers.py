@@ -26,11 +26,11 @@ def bitset_of(sorted_vals):
     return base, words
 
 
-def graph_counts(ctx, src, dst, shape, orders, layouts=((32, 32),)):
+def graph_counts(ctx, src, dst, shape, orders, layouts=((32, 32),), isect_impl=0):
     """COUNT of a graph pattern on the GPU under every (order, layout)."""
     from paper_1708_07859_b300 import lh
     s, d = dev_u32(src), dev_u32(dst)
-    g = lh.GraphJoin(ctx, s, d, shape)
+    g = lh.GraphJoin(ctx, s, d, shape, isect_impl=isect_impl)
     out = {}
     try:
         for lay in layouts:

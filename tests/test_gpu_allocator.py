@@ -44,3 +44,46 @@ def test_joins_on_torch_allocator(orc, lhlib):
         assert e.value.status == lh.EUNSUPPORTED
     finally:
         ctx.close()
+
+
+def test_refusing_allocator_reports_enomem_and_leaks_nothing(orc, lhlib):
+    """An allocator that refuses (returns NULL) makes the call fail with
+    LH_ENOMEM; whatever the call had already allocated is handed back, and
+    the context works again once the allocator gives memory."""
+    import torch
+    lh = lhlib
+    inner = lh.torch_allocator_fns()
+    state = {"left": None, "refused": 0}
+
+    def alloc(nbytes, stream, user):
+        if state["left"] is not None:
+            if state["left"] == 0:
+                state["refused"] += 1
+                return None
+            state["left"] -= 1
+        return inner.alloc(nbytes, stream, user)
+
+    fns = lh.AllocFns(lh.ALLOC_FN(alloc), inner.free, None)
+    ctx = lh.Context(allocator=fns)
+    try:
+        s, d = gen.gnm_edges(3000, 40000, 64)
+        ds, dd = dev_u32(s), dev_u32(d)
+        want = orc.triangle_count(s, d)
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        for k in (0, 1, 3, 6):
+            state["left"], state["refused"] = k, 0
+            g = lh.GraphJoin(ctx, ds, dd, "triangle")
+            with pytest.raises(lh.LHError) as e:
+                g.run(lh.make_plan([0, 1, 2]))
+            assert e.value.status == lh.ENOMEM and state["refused"] >= 1
+            g.free()
+            ctx.sync()
+            torch.cuda.synchronize()
+            assert torch.cuda.memory_allocated() == before, k
+        state["left"] = None
+        g = lh.GraphJoin(ctx, ds, dd, "triangle")
+        assert g.run(lh.make_plan([0, 1, 2]))[0] == want
+        g.free()
+    finally:
+        ctx.close()

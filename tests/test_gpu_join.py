@@ -101,3 +101,62 @@ def test_wrong_trie_order_is_rejected(ctx, lhlib):
     assert r.wait().count == 15
     r.free()
     fwd.free()
+
+
+PAIR_LAYOUTS = ((0, 0), (32, 32), (8, 8), (128, 128))
+
+
+@pytest.mark.parametrize("shape", ["triangle", "cycle4", "lollipop"])
+def test_last_attribute_pair_count_matches_probe_and_oracle(ctx, orc, shape):
+    """The count-only pair path at the last attribute (merge path, or scans
+    probing a bitset / searching a uint set, in work items spread over
+    warps) against the one-thread-per-candidate probe path and the oracle,
+    on a power-law graph whose hub sets take every layout."""
+    from paper_1708_07859_b300 import lh
+    src, dst = gen.chung_lu_edges(5000, 60000, 2.1, 31)
+    want = orc.GRAPH_COUNT[shape](src, dst)
+    n_attrs = 3 if shape == "triangle" else 4
+    orders = [tuple(range(n_attrs)), tuple(reversed(range(n_attrs)))]
+    auto = graph_counts(ctx, src, dst, shape, orders, PAIR_LAYOUTS, isect_impl=lh.ISECT_AUTO)
+    probe = graph_counts(ctx, src, dst, shape, orders, PAIR_LAYOUTS, isect_impl=lh.ISECT_PROBE)
+    assert set(auto.values()) == {want}, (want, auto)
+    assert set(probe.values()) == {want}, (want, probe)
+
+
+@pytest.mark.parametrize("n", [33, 97, 300])
+def test_last_attribute_pair_count_on_complete_graphs(ctx, n):
+    """K_n: every set of the last attribute is a contiguous run, so uint
+    layouts merge and bitset layouts probe; sizes straddle the 32-element
+    threshold of the pair path."""
+    s, d = gen.complete_graph(n)
+    got = graph_counts(ctx, s, d, "triangle", [(0, 1, 2), (2, 1, 0)], PAIR_LAYOUTS)
+    assert set(got.values()) == {math.comb(n, 3)}
+    got = graph_counts(ctx, s, d, "cycle4", [(0, 1, 2, 3)], ((0, 0), (32, 32)))
+    assert set(got.values()) == {math.comb(n, 4)}
+
+
+def test_pair_item_list_overflow_keeps_counts_exact(ctx):
+    """K_3000 triangles (4.5M edges): a last-attribute chunk of 2^22 entries
+    asks for more work items than the list holds, so some entries fall back
+    to the probe path within the same launch; the count stays C(3000, 3)."""
+    s, d = gen.complete_graph(3000)
+    got = graph_counts(ctx, s, d, "triangle", [(0, 1, 2)], ((0, 0), (32, 32)))
+    assert set(got.values()) == {math.comb(3000, 3)}
+
+
+def test_visited_counts_pair_path_reads(ctx, lhlib):
+    """`visited` includes the elements the pair path reads (a triangle query
+    on K_200 sends every large last-attribute pair there)."""
+    s, d = gen.complete_graph(200)
+    out = {}
+    for impl in (lhlib.ISECT_AUTO, lhlib.ISECT_PROBE):
+        g = lhlib.GraphJoin(ctx, dev_u32(s), dev_u32(d), "triangle", isect_impl=impl)
+        plan = lhlib.make_plan([0, 1, 2], bs_ratio=0)
+        tries, q = g._bind(plan, (0, 0))
+        r = ctx.join_aggregate(q, plan, tries)
+        v = r.wait()
+        out[impl] = (int(v.count), int(v.visited))
+        r.free()
+        g.free()
+    assert out[lhlib.ISECT_AUTO][0] == out[lhlib.ISECT_PROBE][0] == math.comb(200, 3)
+    assert out[lhlib.ISECT_AUTO][1] > 0 and out[lhlib.ISECT_PROBE][1] > 0
