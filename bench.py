@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the planner and batched-launch comparisons")
     ap.add_argument("--extras-only", action="store_true", help="run only the WCOJ extras (no headline step)")
     ap.add_argument("--only", default="", help="comma list of extras to run alone: triangle, star, batched, "
-                                               "planner, ghd, dense_mv, groupby_key, fig4a")
+                                               "planner, ghd, dense_mv, groupby_key, fig4a, pairs, dense")
     return ap.parse_args()
 
 
@@ -349,6 +349,35 @@ def gen_seed(k):
 
 # ------------------------------------------------ WCOJ extras (configs 1, 3, 4)
 
+def dense_gemm(ctx, lh, reps=10):
+    """The 4096^3 dense block alone (split, bf16 tcgen05 GEMM with the
+    refinement products, fp32 and fp64 outputs), k_dense_gemm's launches
+    timed by trace events: TFLOP/s over the three bf16 products against the
+    measured bf16 burst peak (a kernel timed in isolation)."""
+    import torch
+    from paper_1708_07859_b300 import inputs as gen
+    Dm = torch.from_numpy(gen.dense_matrix(DENSE, DENSE, gen.SEED_BASE + 21)).cuda()
+    Dn = torch.from_numpy(gen.dense_matrix(DENSE, DENSE, gen.SEED_BASE + 22)).cuda()
+    C32 = torch.empty(DENSE, DENSE, dtype=torch.float32, device="cuda")
+    C64 = torch.empty(DENSE, DENSE, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.dense_matmul(Dm, Dn, C32, C64)
+    ctx.sync()
+    ctx.trace(True)
+    ctx.trace_only("k_dense_gemm")
+    ctx.trace_reset()
+    for _ in range(reps):
+        ctx.dense_matmul(Dm, Dn, C32, C64)
+    launches, total_ms = ctx.trace_read()["k_dense_gemm"]
+    ctx.trace_only(None)
+    ctx.trace(False)
+    ms = total_ms / launches
+    flops = 3 * 2.0 * DENSE ** 3
+    peak = load_peaks()[1]
+    return {"m": DENSE, "n": DENSE, "k": DENSE, "ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
+            "frac_bf16_burst": flops / (ms / 1e3) / 1e12 / peak}
+
+
 def dense_mv(ctx, lh, hbm_peak, l2, n=16384, reps=10):
     """y = A x for the dense 16384 x 16384 relation (the largest of the
     paper's DMV sizes; A is 1 GiB), L2 flushed before each launch: kernel
@@ -442,11 +471,26 @@ def triangle_wcoj(ctx, lh, reps=50):
         t0 = time.perf_counter()
         g.run(plan)
         ts.append(time.perf_counter() - t0)
-    g.free()
     us = statistics.median(ts) * 1e6
+    # the same query as a one-query batch: one graph-captured persistent
+    # launch (no per-attribute host round trips), count read back each time
+    b = lh.Batch(ctx, [(0, g.trie((0, 1)))])
+    b.run()
+    bcnt = int(b.result()[0])
+    tb = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        b.run()
+        b.result()
+        tb.append(time.perf_counter() - t0)
+    b.free()
+    g.free()
+    ub = statistics.median(tb) * 1e6
     return {"graph": {"n": 4096, "m": int(s.size)}, "count": cnt, "elements": el, "visited": visited,
             "us_per_join": us,
-            "gelem_s": el / (us / 1e6) / 1e9, "roofline": "not meaningful (tries L2-resident; latency-bound)"}
+            "gelem_s": el / (us / 1e6) / 1e9,
+            "batched_form": {"us_per_join": ub, "count": bcnt, "gelem_s": el / (ub / 1e6) / 1e9},
+            "roofline": "not meaningful (tries L2-resident; latency-bound)"}
 
 
 def star_join(ctx, lh, hbm_peak, sels=(0.01, 0.05, 0.2), reps=5):
@@ -666,6 +710,33 @@ def planner_compare(ctx, lh, graphs=1):
     return out
 
 
+def pair_isect(ctx, lh, reps=3):
+    """The last attribute's count-only intersection of two sets, by warps
+    over work items (merge path / scan and probe, ISECT_AUTO) against one
+    thread per candidate (ISECT_PROBE): triangle, 4-cycle and lollipop COUNT
+    under the cost plan on the first held-out 2^22-edge Chung-Lu graph
+    (n = 2^19, exponent 2.1).  ms are engine events (lh_plan_time), counts
+    must agree; Gelem/s = input set elements of the join / time."""
+    from paper_1708_07859_b300 import planner
+    s, d = planner.eval_graphs(1)[0]
+    out = {"graph": {"kind": "chung_lu", "n": 1 << 19, "m": int(s.size), "beta": 2.1}}
+    sd, dd = lh.to_device_u32(s), lh.to_device_u32(d)
+    for shape in ("triangle", "cycle4", "lollipop"):
+        rec = {}
+        for name, impl in (("pairs", lh.ISECT_AUTO), ("probe", lh.ISECT_PROBE)):
+            g = lh.GraphJoin(ctx, sd, dd, shape, isect_impl=impl)
+            plan = g.plan()
+            ms = g.time_plan(plan, budget_ms=0.0, repeats=reps)
+            cnt, el = g.run(plan, layout=lh.plan_layout(plan))
+            rec[name] = {"ms": ms, "count": cnt, "elements": el, "gelem_s": el / (ms / 1e3) / 1e9,
+                         "order": plan.order_list(), "layout": [int(plan.bs_ratio), int(plan.bs_ratio_inner)]}
+            g.free()
+        rec["identical_counts"] = rec["pairs"]["count"] == rec["probe"]["count"]
+        rec["speedup"] = rec["probe"]["ms"] / rec["pairs"]["ms"]
+        out[shape] = rec
+    return out
+
+
 def dram_traffic(kernel, rows):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel`
     from the committed ncu capture (profiles/dram_traffic.json), scaled to
@@ -763,7 +834,7 @@ def wcoj_extras(ctx, lh, hbm, l2):
     and the planner comparison."""
     return {"triangle": triangle_wcoj(ctx, lh), "star": star_join(ctx, lh, hbm),
             "batched": batched_compare(ctx, lh, hbm, l2), "planner": planner_compare(ctx, lh),
-            "ghd": ghd_compare(ctx, lh), "dense_mv": dense_mv(ctx, lh, hbm, l2),
+            "ghd": ghd_compare(ctx, lh), "dense_mv": dense_mv(ctx, lh, hbm, l2), "pairs": pair_isect(ctx, lh),
             "groupby_key": groupby_key(ctx, lh)}
 
 
@@ -785,7 +856,8 @@ def main():
         run = {"triangle": lambda: triangle_wcoj(ctx, lh), "star": lambda: star_join(ctx, lh, hbm),
                "batched": lambda: batched_compare(ctx, lh, hbm, l2), "planner": lambda: planner_compare(ctx, lh),
                "ghd": lambda: ghd_compare(ctx, lh), "dense_mv": lambda: dense_mv(ctx, lh, hbm, l2),
-               "groupby_key": lambda: groupby_key(ctx, lh),
+               "groupby_key": lambda: groupby_key(ctx, lh), "pairs": lambda: pair_isect(ctx, lh),
+               "dense": lambda: dense_gemm(ctx, lh),
                "fig4a": lambda: intersect_fig4a(ctx, lh, hbm, l2)}
         print(json.dumps({k: run[k]() for k in args.only.split(",")}))
         ctx.close()
