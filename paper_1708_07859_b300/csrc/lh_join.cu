@@ -19,7 +19,10 @@
 // already knows, so step 1 and the scan are skipped there.
 // The candidate space is cut into chunks of at most `cap` candidates, so the
 // frontier memory is bounded whatever the output size; each chunk recurses
-// before the next is expanded (depth-first over chunks).
+// before the next is expanded (depth-first over chunks).  A chunk of at most
+// kPadFrontierMax candidates hands its survivor count to the next depth on
+// the device (that depth runs over the chunk's capacity, padding sized 0),
+// so the host reads back one candidate total per depth.
 #include <chrono>
 #include <cmath>
 
@@ -30,6 +33,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr uint32_t kSmemGroupsMax = 1024;
 constexpr uint64_t kLastChunk = 1ull << 28;   // candidates per last-attribute launch
+constexpr uint32_t kPadFrontierMax = 1u << 18;  // chunks up to this size pass their survivor count on the device
 constexpr int kMaxG = LH_MAX_GROUP;
 constexpr uint32_t kPrivSlots = 256;                 // per-warp private GROUP BY table
 constexpr unsigned long long kPrivEmpty = ~0ull;
@@ -295,12 +299,21 @@ __device__ __forceinline__ uint32_t warp_merge_count(const uint32_t *A, uint32_t
     return cnt;
 }
 
-__global__ void k_sizes(JQuery q, uint32_t d, const uint32_t *posF, uint32_t nF, uint32_t capF,
-                        uint32_t *size, uint8_t *drv, unsigned long long *elems, uint64_t *items,
+// nF_dev, when given, holds the frontier's real size (the previous depth's
+// survivor counter, never read back to the host); entries from there up to
+// nF are padding and get size 0.
+__global__ void k_sizes(JQuery q, uint32_t d, const uint32_t *posF, uint32_t nF, const uint32_t *nF_dev,
+                        uint32_t capF, uint32_t *size, uint8_t *drv, unsigned long long *elems, uint64_t *items,
                         unsigned long long *n_items, uint64_t cap_items) {
     const JDepth &D = q.D[d];
+    const uint32_t n_real = nF_dev ? min(__ldg(nF_dev), nF) : nF;
     uint64_t local = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+        if (i >= n_real) {
+            size[i] = 0;
+            drv[i] = 0;
+            continue;
+        }
         uint32_t best = 0xFFFFFFFFu, bi = 0xFF;
         uint32_t flat_n = 0xFFFFFFFFu, flat_p = 0xFF;
         for (uint32_t p = 0; p < D.np; ++p) {
@@ -721,7 +734,10 @@ struct Driver {
         return LH_OK;
     }
 
-    lh_status run(uint32_t d, const uint32_t *posF, const uint32_t *gvF, uint32_t nF, uint32_t capF) {
+    // nF: the frontier's size, or an upper bound when nF_dev (a device
+    // counter holding the real size) is given
+    lh_status run(uint32_t d, const uint32_t *posF, const uint32_t *gvF, uint32_t nF, uint32_t capF,
+                  const uint32_t *nF_dev = nullptr) {
         if (nF == 0) return LH_OK;
         LH_TRY(check_time());
         uint32_t *size = nullptr;
@@ -765,7 +781,7 @@ struct Driver {
             rb[0] = best;
         } else if (s == LH_OK) {
             unsigned g = (unsigned)std::min<uint64_t>(lh_blocks(nF, kThreads), (uint64_t)ctx->num_sms * 8);
-            LH_TRACED(ctx, "k_sizes", k_sizes<<<g, kThreads, 0, ctx->stream>>>(q, d, posF, nF, capF, size, drvb,
+            LH_TRACED(ctx, "k_sizes", k_sizes<<<g, kThreads, 0, ctx->stream>>>(q, d, posF, nF, nF_dev, capF, size, drvb,
                                                      (unsigned long long *)r->d_elems, items,
                                                      (unsigned long long *)(off + nF + 1), cap_items));
             s = lh_scan_u32_to_u64(ctx, size, off, nF);
@@ -832,8 +848,15 @@ struct Driver {
                     cudaError_t e = cudaGetLastError();
                     if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "expand: %s", cudaGetErrorString(e));
                 }
-                if (s == LH_OK) s = lh_readback(ctx, counter, sizeof(uint32_t), &nO);
-                if (s == LH_OK) s = run(d + 1, posO, gvO, nO, capO);
+                // a small chunk's survivors are not read back: the next depth
+                // runs over the chunk's capacity and reads the real count on
+                // the device (one host round trip fewer per depth)
+                if (s == LH_OK && capO <= kPadFrontierMax) {
+                    s = run(d + 1, posO, gvO, capO, capO, counter);
+                } else {
+                    if (s == LH_OK) s = lh_readback(ctx, counter, sizeof(uint32_t), &nO);
+                    if (s == LH_OK) s = run(d + 1, posO, gvO, nO, capO);
+                }
                 lh_free(ctx, posO);
                 lh_free(ctx, gvO);
                 lh_free(ctx, counter);
@@ -1054,10 +1077,10 @@ lh_status lh_run_generic(lh_ctx *ctx, const lh_query *q, const lh_plan_t *plan,
     dr.grid_expand = (unsigned)(ctx->num_sms * per_sm);
     // results
     r->ngroups = (dr.mode_last == M_AGG && jq.gmode == G_DENSE) ? jq.ngroups : 0;
-    LH_TRY(res_alloc(ctx, r, &r->d_count, 1));
-    LH_TRY(res_alloc(ctx, r, &r->d_elems, 2));   // [0] elements, [1] elements read by k_count_pairs
-    LH_CU(cudaMemsetAsync(r->d_count, 0, sizeof(uint64_t), ctx->stream));
-    LH_CU(cudaMemsetAsync(r->d_elems, 0, 2 * sizeof(uint64_t), ctx->stream));
+    // count, elements, elements read by k_count_pairs: one block, read back at once
+    LH_TRY(res_alloc(ctx, r, &r->d_count, 3));
+    r->d_elems = r->d_count + 1;
+    LH_CU(cudaMemsetAsync(r->d_count, 0, 3 * sizeof(uint64_t), ctx->stream));
     if (r->ngroups) {
         LH_TRY(res_alloc(ctx, r, &r->d_gsum, r->ngroups));
         LH_TRY(res_alloc(ctx, r, &r->d_gcount, r->ngroups));
@@ -1200,8 +1223,16 @@ extern "C" lh_status lh_result_wait(lh_ctx *ctx, lh_result *r, lh_result_view *v
         r->ngroups = (uint32_t)G;
     }
     uint64_t cnt = 0, el[2] = {0, 0};
-    if (r->d_count) LH_CU(cudaMemcpy(&cnt, r->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
-    if (r->d_elems) LH_CU(cudaMemcpy(el, r->d_elems, sizeof(el), cudaMemcpyDeviceToHost));
+    if (r->d_count && r->d_elems == r->d_count + 1) {
+        uint64_t w[3];
+        LH_CU(cudaMemcpy(w, r->d_count, sizeof(w), cudaMemcpyDeviceToHost));
+        cnt = w[0];
+        el[0] = w[1];
+        el[1] = w[2];
+    } else {
+        if (r->d_count) LH_CU(cudaMemcpy(&cnt, r->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
+        if (r->d_elems) LH_CU(cudaMemcpy(el, r->d_elems, sizeof(el), cudaMemcpyDeviceToHost));
+    }
     v->elements = el[0];
     v->visited = r->visited + el[1];
     v->count = cnt + r->host_count;
