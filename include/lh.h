@@ -605,6 +605,22 @@ lh_status lh_batch_elements(lh_ctx *ctx, lh_batch *b, uint64_t *elements);
 lh_status lh_batch_autotune(lh_ctx *ctx, uint32_t n, const lh_batch_query *qs, uint64_t *counts,
                             lh_batch_tuning *best, float *best_ms);
 
+/* The batched form of lh_join_aggregate: n queries with their plans;
+ * tries[i] is query i's host array of tries (as for lh_join_aggregate);
+ * out: host array of n result handles, each read with lh_result_wait and
+ * released with lh_result_free as usual.  Queries the persistent kernel
+ * serves -- COUNT without GROUP BY of the triangle R(a,b) S(b,c) T(a,c) or of
+ * the six-edge 4-clique over one relation, in the identity attribute order,
+ * every edge on the same trie built in key order {0, 1} -- are packed into
+ * one graph-captured launch (tuning as for lh_batch_create, NULL =
+ * defaults) and are complete when the call returns (one synchronisation for
+ * all of them; their result views report count only).  Every other query
+ * runs through lh_join_aggregate in turn.  On failure no result is
+ * returned (all of out[] is NULL). */
+lh_status lh_join_aggregate_batch(lh_ctx *ctx, uint32_t n, const lh_query *qs, const lh_plan_t *plans,
+                                  lh_trie *const *const *tries, const lh_batch_tuning *tuning,
+                                  lh_result **out);
+
 /* ------------------------------------ learned cost model (no paper counterpart) */
 
 /* MLP n_in -> hidden -> hidden -> 1 with ReLU, fp32, parameters in one flat

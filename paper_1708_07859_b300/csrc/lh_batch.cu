@@ -18,7 +18,7 @@
 #include <chrono>
 #include <cmath>
 
-#include "lh_internal.cuh"
+#include "lh_join.cuh"
 
 struct lh_batch {
     uint32_t n = 0;
@@ -328,5 +328,102 @@ extern "C" lh_status lh_batch_autotune(lh_ctx *ctx, uint32_t n_all, const lh_bat
     if (s != LH_OK) return s;
     *best = cands[0].t;
     if (best_ms) *best_ms = (float)cands[0].ms;
+    return LH_OK;
+}
+
+// ------------------------------------------------- batched join-aggregate
+// The batched form of lh_join_aggregate: queries whose shape the persistent
+// kernel serves -- the triangle or 4-clique COUNT over one edge relation, in
+// the identity attribute order, its trie built in key order {0, 1} -- go
+// into one captured launch; the rest run through lh_join_aggregate.
+
+namespace {
+
+// 1: triangle, 2: 4-clique, 0: not a batch shape
+uint32_t batch_shape(const lh_query &q, const lh_plan_t &p, lh_trie *const *tries, const lh_trie **graph) {
+    if (q.semiring != LH_COUNT_U64 || q.n_group != 0) return 0;
+    const uint32_t k = q.n_attrs;
+    if (!((k == 3 && q.n_edges == 3) || (k == 4 && q.n_edges == 6))) return 0;
+    if (p.n_attrs != k) return 0;
+    for (uint32_t i = 0; i < k; ++i)
+        if (p.order[i] != i) return 0;
+    const int32_t slot = q.edges[0].trie_slot;
+    if (slot < 0 || !tries || !tries[slot]) return 0;
+    uint32_t seen = 0;   // bit (a * 4 + b) for pattern edge (a, b), a < b
+    for (uint32_t e = 0; e < q.n_edges; ++e) {
+        const lh_edge &E = q.edges[e];
+        if (E.trie_slot != slot || E.nattrs != 2 || E.flat) return 0;
+        const uint32_t a = E.attrs[0], b = E.attrs[1];
+        if (a >= b || b >= k) return 0;
+        seen |= 1u << (a * 4 + b);
+    }
+    uint32_t want = 0;
+    for (uint32_t a = 0; a < k; ++a)
+        for (uint32_t b = a + 1; b < k; ++b) want |= 1u << (a * 4 + b);
+    if (seen != want) return 0;
+    const lh_trie *t = tries[slot];
+    if (t->nlevels != 2 || t->key_order[0] != 0 || t->key_order[1] != 1) return 0;
+    *graph = t;
+    return k == 3 ? 1u : 2u;
+}
+
+}  // namespace
+
+extern "C" lh_status lh_join_aggregate_batch(lh_ctx *ctx, uint32_t n, const lh_query *qs, const lh_plan_t *plans,
+                                             lh_trie *const *const *tries, const lh_batch_tuning *tuning,
+                                             lh_result **out) {
+    if (!ctx) return LH_EINVAL;
+    if (n && (!qs || !plans || !tries || !out)) return lh_fail(ctx, LH_EINVAL, "null argument");
+    for (uint32_t i = 0; i < n; ++i) out[i] = nullptr;
+    std::vector<lh_batch_query> bq;
+    std::vector<uint32_t> bidx;
+    for (uint32_t i = 0; i < n; ++i) {
+        const lh_trie *g = nullptr;
+        const uint32_t shape = batch_shape(qs[i], plans[i], tries[i], &g);
+        if (shape) {
+            bq.push_back(lh_batch_query{shape == 1 ? (uint32_t)LH_BATCH_TRIANGLE : (uint32_t)LH_BATCH_CLIQUE4, g});
+            bidx.push_back(i);
+        }
+    }
+    auto fail = [&](lh_status st) {
+        for (uint32_t i = 0; i < n; ++i)
+            if (out[i]) {
+                lh_result_free(ctx, out[i]);
+                out[i] = nullptr;
+            }
+        return st;
+    };
+    // the shapes the persistent kernel serves: one launch, one readback
+    if (!bq.empty()) {
+        const uint32_t nb = (uint32_t)bq.size();
+        uint64_t *counts = nullptr;
+        lh_batch *b = nullptr;
+        lh_status s = lh_alloc(ctx, &counts, nb);
+        if (s == LH_OK) s = lh_batch_create(ctx, nb, bq.data(), tuning, counts, &b);
+        if (s == LH_OK) s = lh_batch_run(ctx, b);
+        std::vector<uint64_t> hc(nb, 0);
+        if (s == LH_OK) {
+            cudaError_t e = cudaMemcpyAsync(hc.data(), counts, nb * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "batch counts: %s", cudaGetErrorString(e));
+        }
+        if (s == LH_OK) s = lh_sync(ctx);
+        if (b) lh_batch_free(ctx, b);
+        lh_free(ctx, counts);
+        if (s != LH_OK) return fail(s);
+        for (uint32_t j = 0; j < nb; ++j) {
+            lh_result *r = new lh_result();
+            r->exec = LH_EXEC_GENERIC;
+            r->semiring = LH_COUNT_U64;
+            r->host_count = hc[j];
+            out[bidx[j]] = r;
+        }
+    }
+    // every other query through the generic entry point
+    for (uint32_t i = 0; i < n; ++i) {
+        if (out[i]) continue;
+        lh_status s = lh_join_aggregate(ctx, &qs[i], &plans[i], tries[i], &out[i]);
+        if (s != LH_OK) return fail(s);
+    }
     return LH_OK;
 }

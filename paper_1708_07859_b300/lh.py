@@ -179,6 +179,8 @@ EXPORTS = {
     "lh_edge_key_order": [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p],
     "lh_plan_explain": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lh_join_aggregate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lh_join_aggregate_batch": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p],
     "lh_join_to_trie": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
                         C.c_void_p],
     "lh_build_trie_where": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_uint32,
@@ -440,6 +442,21 @@ class Context:
         out = C.c_void_p()
         self._check(lib().lh_join_aggregate(self.h, C.byref(q), C.byref(plan), arr, C.byref(out)))
         return Result(self, out)
+
+    def join_aggregate_batch(self, items, tuning=None):
+        """lh_join_aggregate_batch over items = [(query, plan, tries), ...]:
+        triangle / 4-clique COUNT queries of the persistent kernel's shape go
+        into one launch, the rest run one by one; a list of Results."""
+        n = len(items)
+        qs = (Query * max(1, n))(*[q for q, _, _ in items])
+        ps = (Plan * max(1, n))(*[p for _, p, _ in items])
+        arrs = [(C.c_void_p * max(1, len(t)))(*[x.h.value if x is not None else None for x in t]) for _, _, t in items]
+        tp = (C.c_void_p * max(1, n))(*[C.cast(a, C.c_void_p) for a in arrs])
+        out = (C.c_void_p * max(1, n))()
+        tun = BatchTuning(*tuning) if tuning is not None else None
+        self._check(lib().lh_join_aggregate_batch(self.h, n, qs, ps, tp, C.byref(tun) if tun is not None else None,
+                                                  out))
+        return [Result(self, C.c_void_p(out[i])) for i in range(n)]
 
     def dense_matmul(self, A, B, c_bf16, c_refined=None):
         m, k = A.shape

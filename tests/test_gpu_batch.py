@@ -114,3 +114,50 @@ def test_batch_full_size_vs_oracle(ctx, orc, lhlib, full_batch_graphs):
         assert np.array_equal(again, want)
     for t in tries:
         t.free()
+
+
+def test_join_aggregate_batch_mixes_kernel_and_generic_queries(ctx, orc, lhlib):
+    """lh_join_aggregate_batch: triangle and 4-clique COUNT queries in the
+    identity order share one persistent launch; a 4-cycle, a lollipop and a
+    triangle under another order run through the generic driver; every count
+    equals the oracle's and the one-by-one lh_join_aggregate's."""
+    lh = lhlib
+    graphs = [gen.gnm_edges(300 + 100 * i, 2500 + 700 * i, 900 + i) for i in range(3)]
+    graphs.append(gen.chung_lu_edges(3000, 30000, 2.1, 904))
+    joins, items, want = [], [], []
+    for i, (s, d) in enumerate(graphs):
+        for shape, order in (("triangle", [0, 1, 2]), ("clique4", [0, 1, 2, 3]), ("cycle4", [0, 1, 2, 3]),
+                             ("triangle", [2, 0, 1]), ("lollipop", [0, 2, 1, 3])):
+            g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), shape)
+            joins.append(g)
+            plan = lh.make_plan(order)
+            tries, q = g._bind(plan, (32, 32))
+            items.append((q, plan, tries))
+            want.append(orc.GRAPH_COUNT[shape](s, d))
+    res = ctx.join_aggregate_batch(items)
+    got = [int(r.wait().count) for r in res]
+    for r in res:
+        r.free()
+    one = []
+    for q, plan, tries in items:
+        r = ctx.join_aggregate(q, plan, tries)
+        one.append(int(r.wait().count))
+        r.free()
+    for g in joins:
+        g.free()
+    assert got == want
+    assert one == want
+
+
+def test_join_aggregate_batch_empty_and_tuned(ctx, orc, lhlib):
+    lh = lhlib
+    assert ctx.join_aggregate_batch([]) == []
+    s, d = gen.gnm_edges(500, 6000, 910)
+    g = lh.GraphJoin(ctx, dev_u32(s), dev_u32(d), "triangle")
+    plan = lh.make_plan([0, 1, 2])
+    tries, q = g._bind(plan, (32, 32))
+    res = ctx.join_aggregate_batch([(q, plan, tries)] * 5, tuning=(64, 32, 2, 0))
+    assert [int(r.wait().count) for r in res] == [orc.triangle_count(s, d)] * 5
+    for r in res:
+        r.free()
+    g.free()
