@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the planner and batched-launch comparisons")
     ap.add_argument("--extras-only", action="store_true", help="run only the WCOJ extras (no headline step)")
     ap.add_argument("--only", default="", help="comma list of extras to run alone: triangle, star, batched, "
-                                               "planner, ghd, dense_mv, groupby_key, fig4a, pairs, dense")
+                                               "planner, ghd, dense_mv, groupby_key, fig4a, pairs, dense, learned_batched")
     return ap.parse_args()
 
 
@@ -706,8 +706,74 @@ def planner_compare(ctx, lh, graphs=1):
         out[shape + "_mean_regret"] = {
             "learned": statistics.mean(g[shape]["regret_learned"] for g in out["graphs"]),
             "cost": statistics.mean(g[shape]["regret_cost"] for g in out["graphs"])}
+    out["learned_batched_vs_cost_plain"] = learned_batched(ctx, lh, planner, model)
     model.free()
     return out
+
+
+def learned_batched_only(ctx, lh):
+    from paper_1708_07859_b300 import planner
+    model = planner.load_model(ctx)
+    try:
+        return learned_batched(ctx, lh, planner, model)
+    finally:
+        model.free()
+
+
+def learned_batched(ctx, lh, planner, model, reps=3):
+    """The learned plans in the batched form against the plain cost-model
+    plans: the triangle, 4-cycle and lollipop COUNT queries over the first
+    held-out 2^22-edge graph, (a) each under the cost model's plan through its
+    own lh_join_aggregate + lh_result_wait, (b) all under the learned model's
+    plans in one lh_join_aggregate_batch call (queries of the persistent
+    kernel's shape share its launch; the others run through the generic driver
+    inside the call) and their waits.  Wall-clock ms (host round trips
+    included, tries built beforehand); the counts must be identical."""
+    s, d = planner.eval_graphs(1)[0]
+    sd, dd = lh.to_device_u32(s), lh.to_device_u32(d)
+    joins, plain, batched = [], [], []
+    for shape in ("triangle", "cycle4", "lollipop"):
+        g = lh.GraphJoin(ctx, sd, dd, shape)
+        joins.append(g)
+        pc = g.plan()
+        pl = g.plan(lh.PLANNER_LEARNED, model=model, opts=lh.plan_opts(planner.POLICIES, per_level=True))
+        tc, qc = g._bind(pc, lh.plan_layout(pc))
+        tl, ql = g._bind(pl, lh.plan_layout(pl))
+        plain.append((qc, pc, tc))
+        batched.append((ql, pl, tl))
+
+    def run_plain():
+        cnt = []
+        for q, p, t in plain:
+            r = ctx.join_aggregate(q, p, t)
+            cnt.append(int(r.wait().count))
+            r.free()
+        return cnt
+
+    def run_batched():
+        res = ctx.join_aggregate_batch(batched)
+        cnt = [int(r.wait().count) for r in res]
+        for r in res:
+            r.free()
+        return cnt
+
+    c_plain, c_batched = run_plain(), run_batched()      # warm
+    tp, tb = [], []
+    for _ in range(reps):
+        ctx.sync()
+        t0 = time.perf_counter()
+        run_plain()
+        tp.append((time.perf_counter() - t0) * 1e3)
+        ctx.sync()
+        t0 = time.perf_counter()
+        run_batched()
+        tb.append((time.perf_counter() - t0) * 1e3)
+    for g in joins:
+        g.free()
+    mp, mb = statistics.median(tp), statistics.median(tb)
+    return {"queries": ["triangle", "cycle4", "lollipop"], "cost_plain_ms": mp, "learned_batched_ms": mb,
+            "speedup": mp / mb, "identical_counts": c_plain == c_batched,
+            "learned_orders": [list(p.order_list()) for _, p, _ in batched]}
 
 
 def pair_isect(ctx, lh, reps=3):
@@ -857,7 +923,7 @@ def main():
                "batched": lambda: batched_compare(ctx, lh, hbm, l2), "planner": lambda: planner_compare(ctx, lh),
                "ghd": lambda: ghd_compare(ctx, lh), "dense_mv": lambda: dense_mv(ctx, lh, hbm, l2),
                "groupby_key": lambda: groupby_key(ctx, lh), "pairs": lambda: pair_isect(ctx, lh),
-               "dense": lambda: dense_gemm(ctx, lh),
+               "dense": lambda: dense_gemm(ctx, lh), "learned_batched": lambda: learned_batched_only(ctx, lh),
                "fig4a": lambda: intersect_fig4a(ctx, lh, hbm, l2)}
         print(json.dumps({k: run[k]() for k in args.only.split(",")}))
         ctx.close()
