@@ -271,8 +271,8 @@ def intersect_fig4a(ctx, lh, hbm_peak, l2, reps=5, seed_base=0):
     sparse uint sets (density 1/32).  Every batch holds at least 4x the L2
     (>= 504 MB of set data) and the 256 MB flush buffer is written between
     repetitions, so each launch streams its sets from HBM.  Reports
-    elements/s, algorithmic GB/s of the k_isect launches (sets read once) and
-    the fraction of HBM peak."""
+    elements/s, algorithmic GB/s of the k_isect / k_isect_lean launches (sets
+    read once) and the fraction of HBM peak."""
     import torch
     out = {}
     # name, card, gap, pairs, layouts (0 uint, 1 bitset)
@@ -320,8 +320,11 @@ def intersect_fig4a(ctx, lh, hbm_peak, l2, reps=5, seed_base=0):
         counts = torch.zeros(npairs, dtype=torch.int64, device="cuda")
         ctx.intersect_count_batch(A, B, counts)
         torch.cuda.synchronize()
+        # merge tiles run in k_isect, the other kinds in k_isect_lean: a
+        # batch of one kind launches one of them, timed by its own events
+        kernel = "k_isect" if name.startswith("uint_uint") else "k_isect_lean"
         ctx.trace_reset()
-        ctx.trace_only("k_isect")
+        ctx.trace_only(kernel)
         for _ in range(reps):
             flush_l2(l2)
             ctx.trace(True)
@@ -329,8 +332,10 @@ def intersect_fig4a(ctx, lh, hbm_peak, l2, reps=5, seed_base=0):
             ctx.trace(False)
         tr = ctx.trace_read()
         ctx.trace_only(None)
-        n_l, tot = tr.get("k_isect", (0, 0.0))
-        ms = tot / max(1, n_l)
+        n_l, tot = tr.get(kernel, (0, 0.0))
+        if n_l == 0:
+            raise RuntimeError(f"{name}: no {kernel} launch traced")
+        ms = tot / n_l
         elems = 2 * card * npairs          # set cardinalities (a bitset of density 1/2 holds ~card values)
         gbs = nbytes / (ms / 1e3) / 1e9
         out[name] = {"pairs": npairs, "card": card, "span": span, "set_bytes": nbytes, "ms": ms,

@@ -32,7 +32,7 @@ struct PairPlan {
 __device__ __forceinline__ uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
 __global__ void k_plan(uint32_t npairs, const lh_set *A, const lh_set *B, PairPlan *plan,
-                       uint64_t *tiles) {
+                       uint64_t *tiles, unsigned long long *n_merge = nullptr) {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npairs) return;
     lh_set a = A[p], b = B[p];
@@ -68,6 +68,7 @@ __global__ void k_plan(uint32_t npairs, const lh_set *A, const lh_set *B, PairPl
     }
     plan[p] = pl;
     tiles[p] = nt;
+    if (n_merge && pl.kind == K_MERGE && nt) atomicAdd(n_merge, (unsigned long long)nt);
 }
 
 // merge-path split of diagonal d (ties: A first)
@@ -414,8 +415,10 @@ __device__ __forceinline__ uint32_t sw_split(const uint32_t *a, uint32_t na, con
     return lo;
 }
 
+// merge_only: the probe, uint-cap-bs and bs-cap-bs tiles are left to
+// k_isect_lean (launched beside this kernel) and skipped here.
 __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint64_t total, uint64_t *counts,
-                                                     uint32_t *status) {
+                                                     uint32_t *status, uint32_t merge_only) {
     __shared__ __align__(128) uint32_t la_buf[kBufA];
     __shared__ __align__(128) uint32_t lb_buf[kBufB];
     __shared__ uint32_t pa[kSwz];
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const uint32_t k = threadIdx.x + r * kThreads;
-        xn[r] = ((d.kind & 255u) == K_UBS || (d.kind & 255u) == K_PROBE) && k < d.la ? __ldg(d.a + k) : 0u;
+        xn[r] = !merge_only && ((d.kind & 255u) == K_UBS || (d.kind & 255u) == K_PROBE) && k < d.la ? __ldg(d.a + k) : 0u;
     }
     while (tile < total) {
         const uint64_t next = tile + gridDim.x;
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
         uint32_t x[kItems];
 #pragma unroll
         for (int r = 0; r < kItems; ++r) x[r] = xn[r];
-        if (next < total && ((dn.kind & 255u) == K_UBS || (dn.kind & 255u) == K_PROBE)) {
+        if (!merge_only && next < total && ((dn.kind & 255u) == K_UBS || (dn.kind & 255u) == K_PROBE)) {
 #pragma unroll
             for (int r = 0; r < kItems; ++r) {
                 const uint32_t k = threadIdx.x + r * kThreads;
@@ -510,6 +513,8 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
                     }
                 }
             }
+        } else if (merge_only) {
+            // another kernel counts this tile
         } else if (kind == K_UBS || kind == K_PROBE) {
             if (kind == K_UBS) {
                 uint32_t w[kItems];
@@ -565,6 +570,76 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
     // iteration exists to wait for it), so no copy is in flight here
 }
 
+// Probe, uint-cap-bs and bs-cap-bs tiles need no shared staging, so they run
+// in a kernel of their own whose occupancy is not held down by the merge
+// tiles' shared buffers: more tiles per SM keep more loads in flight (the
+// bs-cap-bs batches are bound by loads in flight).  Tiles of other kinds are
+// skipped (k_isect4 counts the merge tiles).
+constexpr int kLeanCtas = 6;
+
+__global__ void __launch_bounds__(kThreads, kLeanCtas) k_isect_lean(const TileDesc *desc, uint64_t total,
+                                                                    uint64_t *counts) {
+    __shared__ uint32_t red[kThreads / 32];
+    for (uint64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const TileDesc d = desc[tile];
+        const uint32_t kind = d.kind & 255u;
+        if (kind != K_UBS && kind != K_PROBE && kind != K_BB) continue;  // the same for the whole block
+        const uint32_t la = d.la;
+        uint32_t cnt = 0;
+        if (kind == K_BB) {
+            const uint4 *qa = (const uint4 *)d.a;
+            const uint4 *qb = (const uint4 *)d.b;
+            const uint32_t nv = la >> 2;
+            constexpr int kVec = kTile / 4 / kThreads;
+            uint4 xa[kVec], xb[kVec];
+#pragma unroll
+            for (int u = 0; u < kVec; ++u) {
+                const uint32_t k = threadIdx.x + u * kThreads;
+                xa[u] = k < nv ? __ldg(qa + k) : make_uint4(0, 0, 0, 0);
+                xb[u] = k < nv ? __ldg(qb + k) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < kVec; ++u)
+                cnt += __popc(xa[u].x & xb[u].x) + __popc(xa[u].y & xb[u].y) + __popc(xa[u].z & xb[u].z) +
+                       __popc(xa[u].w & xb[u].w);
+        } else {
+            uint32_t x[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const uint32_t k = threadIdx.x + r * kThreads;
+                x[r] = k < la ? __ldg(d.a + k) : 0u;
+            }
+            if (kind == K_UBS) {
+                uint32_t w[kItems];
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) {
+                    const uint32_t k = threadIdx.x + r * kThreads;
+                    const uint32_t dd = x[r] - d.bbase;
+                    const bool in = k < la && x[r] >= d.bbase && (uint64_t)(dd >> 5) < d.bn;
+                    w[r] = in ? __ldg(d.b + (dd >> 5)) : 0u;
+                }
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((x[r] - d.bbase) & 31u)) & 1u;
+            } else {
+#pragma unroll
+                for (int r = 0; r < kItems; ++r) {
+                    const uint32_t k = threadIdx.x + r * kThreads;
+                    if (k >= la) continue;
+                    uint64_t l = 0, h = d.bn;
+                    while (l < h) {
+                        const uint64_t m = (l + h) >> 1;
+                        if (__ldg(d.b + m) < x[r]) l = m + 1;
+                        else h = m;
+                    }
+                    cnt += (l < d.bn && __ldg(d.b + l) == x[r]) ? 1u : 0u;
+                }
+            }
+        }
+        const uint32_t tot = block_sum(cnt, red);
+        if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + d.pair), (unsigned long long)tot);
+    }
+}
+
 }  // namespace
 
 extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
@@ -575,25 +650,44 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
     PairPlan *plan = nullptr;
     uint64_t *tiles = nullptr, *off = nullptr;
     uint64_t ntiles = 0;
+    // off[npairs]: the tile total; off[npairs + 1]: the merge tiles among them
     lh_status s = lh_alloc(ctx, &plan, npairs);
     if (s == LH_OK) s = lh_alloc(ctx, &tiles, npairs);
-    if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)npairs + 1);
+    if (s == LH_OK) s = lh_alloc(ctx, &off, (size_t)npairs + 2);
     if (s == LH_OK) {
         cudaMemsetAsync(counts, 0, npairs * sizeof(uint64_t), ctx->stream);
-        LH_TRACED(ctx, "k_plan", k_plan<<<lh_blocks(npairs, 256), 256, 0, ctx->stream>>>(npairs, a, b, plan, tiles));
+        cudaMemsetAsync(off + npairs + 1, 0, sizeof(uint64_t), ctx->stream);
+        LH_TRACED(ctx, "k_plan", k_plan<<<lh_blocks(npairs, 256), 256, 0, ctx->stream>>>(
+                                     npairs, a, b, plan, tiles, (unsigned long long *)(off + npairs + 1)));
         s = lh_scan_u64_to_u64(ctx, tiles, off, npairs);
     }
-    if (s == LH_OK) s = lh_readback(ctx, off + npairs, sizeof(uint64_t), &ntiles);
+    uint64_t rb[2] = {0, 0};
+    if (s == LH_OK) s = lh_readback(ctx, off + npairs, sizeof(rb), rb);
+    ntiles = rb[0];
+    const uint64_t n_merge = rb[1];
     TileDesc *desc = nullptr;
     if (s == LH_OK) s = lh_alloc(ctx, &desc, ntiles);
     if (s == LH_OK && ntiles) {
         LH_TRACED(ctx, "k_isect_tiles", k_isect_tiles<<<lh_blocks(ntiles, 256, (unsigned)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
                                             npairs, a, b, plan, off, desc));
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect4, kThreads, 0);
-        if (per_sm < 1) per_sm = 1;
-        unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * per_sm);
-        LH_TRACED(ctx, "k_isect", k_isect4<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts, ctx->d_status));
+        // merge tiles in k_isect4 (shared staging), the other kinds in
+        // k_isect_lean; a batch of one kind launches one kernel
+        const bool lean = n_merge < ntiles;
+        if (n_merge) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect4, kThreads, 0);
+            if (per_sm < 1) per_sm = 1;
+            const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * per_sm);
+            LH_TRACED(ctx, "k_isect", k_isect4<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts, ctx->d_status,
+                                                                                   lean ? 1u : 0u));
+        }
+        if (lean) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_lean, kThreads, 0);
+            if (per_sm < 1) per_sm = 1;
+            const unsigned grid = (unsigned)std::min<uint64_t>(ntiles - n_merge, (uint64_t)ctx->num_sms * per_sm);
+            LH_TRACED(ctx, "k_isect_lean", k_isect_lean<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts));
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = lh_fail(ctx, LH_ECUDA, "intersect: %s", cudaGetErrorString(e));
     }
