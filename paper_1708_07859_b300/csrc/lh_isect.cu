@@ -1,7 +1,8 @@
 // Count-only set intersection of many independent pairs (the core operation
 // of an attribute, Section 2.4; the three layout pairs of Section 4.1.1 /
-// Figure 4a).  All pairs are cut into fixed-size tiles and one launch
-// drains every tile of every pair:
+// Figure 4a).  All pairs are cut into fixed-size tiles; merge tiles are
+// drained by one launch of k_isect4 (shared staging), the other kinds by one
+// launch of k_isect_lean (no staging, higher occupancy):
 //   uint cap uint, sizes within 32x: merge path.  Tile t covers diagonals
 //     [t*TILE, (t+1)*TILE) of the pair's merge; the A and B slices it
 //     consumes are staged in shared memory and every thread merges 16
@@ -415,10 +416,10 @@ __device__ __forceinline__ uint32_t sw_split(const uint32_t *a, uint32_t na, con
     return lo;
 }
 
-// merge_only: the probe, uint-cap-bs and bs-cap-bs tiles are left to
-// k_isect_lean (launched beside this kernel) and skipped here.
+// Merge tiles only: the probe, uint-cap-bs and bs-cap-bs tiles of a batch
+// are counted by k_isect_lean (launched beside this kernel) and skipped here.
 __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint64_t total, uint64_t *counts,
-                                                     uint32_t *status, uint32_t merge_only) {
+                                                     uint32_t *status) {
     __shared__ __align__(128) uint32_t la_buf[kBufA];
     __shared__ __align__(128) uint32_t lb_buf[kBufB];
     __shared__ uint32_t pa[kSwz];
@@ -440,12 +441,6 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
     if ((d.kind & 255u) == K_MERGE) {
         stage_merge(d, la_buf, lb_buf, &bar, offa, offb);
         uses++;
-    }
-    uint32_t xn[kItems];   // uint elements of the next probe / uint-cap-bs tile
-#pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        const uint32_t k = threadIdx.x + r * kThreads;
-        xn[r] = !merge_only && ((d.kind & 255u) == K_UBS || (d.kind & 255u) == K_PROBE) && k < d.la ? __ldg(d.a + k) : 0u;
     }
     while (tile < total) {
         const uint64_t next = tile + gridDim.x;
@@ -482,19 +477,6 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
             stage_merge(dn, la_buf, lb_buf, &bar, offa, offb);
             uses++;
         }
-        // a probe / uint-cap-bs tile's uint elements were loaded during the
-        // previous tile (or before the loop); the next tile's are issued
-        // now, so they arrive while this tile is counted
-        uint32_t x[kItems];
-#pragma unroll
-        for (int r = 0; r < kItems; ++r) x[r] = xn[r];
-        if (!merge_only && next < total && ((dn.kind & 255u) == K_UBS || (dn.kind & 255u) == K_PROBE)) {
-#pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const uint32_t k = threadIdx.x + r * kThreads;
-                xn[r] = k < dn.la ? __ldg(dn.a + k) : 0u;
-            }
-        }
         uint32_t cnt = 0;
         if (kind == K_MERGE) {
             const uint32_t s = threadIdx.x * kItems;
@@ -513,52 +495,6 @@ __global__ void __launch_bounds__(kThreads) k_isect4(const TileDesc *desc, uint6
                     }
                 }
             }
-        } else if (merge_only) {
-            // another kernel counts this tile
-        } else if (kind == K_UBS || kind == K_PROBE) {
-            if (kind == K_UBS) {
-                uint32_t w[kItems];
-#pragma unroll
-                for (int r = 0; r < kItems; ++r) {
-                    const uint32_t k = threadIdx.x + r * kThreads;
-                    const uint32_t dd = x[r] - d.bbase;
-                    const bool in = k < la && x[r] >= d.bbase && (uint64_t)(dd >> 5) < d.bn;
-                    w[r] = in ? __ldg(d.b + (dd >> 5)) : 0u;
-                }
-#pragma unroll
-                for (int r = 0; r < kItems; ++r) cnt += (w[r] >> ((x[r] - d.bbase) & 31u)) & 1u;
-            } else {
-#pragma unroll
-                for (int r = 0; r < kItems; ++r) {
-                    const uint32_t k = threadIdx.x + r * kThreads;
-                    if (k >= la) continue;
-                    uint64_t l = 0, h = d.bn;
-                    while (l < h) {
-                        const uint64_t m = (l + h) >> 1;
-                        if (__ldg(d.b + m) < x[r]) l = m + 1;
-                        else h = m;
-                    }
-                    cnt += (l < d.bn && __ldg(d.b + l) == x[r]) ? 1u : 0u;
-                }
-            }
-        } else if (kind == K_BB) {
-            // a tile is at most kTile words = kTile / 4 16-byte vectors per
-            // side: every load of the thread is issued before the ANDs
-            const uint4 *qa = (const uint4 *)d.a;
-            const uint4 *qb = (const uint4 *)d.b;
-            const uint32_t nv = la >> 2;
-            constexpr int kVec = kTile / 4 / kThreads;
-            uint4 xa[kVec], xb[kVec];
-#pragma unroll
-            for (int u = 0; u < kVec; ++u) {
-                const uint32_t k = threadIdx.x + u * kThreads;
-                xa[u] = k < nv ? __ldg(qa + k) : make_uint4(0, 0, 0, 0);
-                xb[u] = k < nv ? __ldg(qb + k) : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int u = 0; u < kVec; ++u)
-                cnt += __popc(xa[u].x & xb[u].x) + __popc(xa[u].y & xb[u].y) + __popc(xa[u].z & xb[u].z) +
-                       __popc(xa[u].w & xb[u].w);
         }
         const uint32_t tot = block_sum(cnt, red);  // ends with a barrier: the padded tile is free again
         if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long *)(counts + d.pair), (unsigned long long)tot);
@@ -678,8 +614,7 @@ extern "C" lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, cons
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect4, kThreads, 0);
             if (per_sm < 1) per_sm = 1;
             const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * per_sm);
-            LH_TRACED(ctx, "k_isect", k_isect4<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts, ctx->d_status,
-                                                                                   lean ? 1u : 0u));
+            LH_TRACED(ctx, "k_isect", k_isect4<<<grid, kThreads, 0, ctx->stream>>>(desc, ntiles, counts, ctx->d_status));
         }
         if (lean) {
             int per_sm = 0;
