@@ -128,3 +128,48 @@ def test_sql_refusals(text, msg):
     with pytest.raises(sql.SQLError) as e:
         sql.translate(text, CATALOG)
     assert msg in str(e.value)
+
+
+@pytest.mark.parametrize("cond,want", [
+    ("o.o_date = 300", (300, 300)),
+    ("o.o_date < 300", (-2 ** 31, 299)),
+    ("o.o_date <= 300", (-2 ** 31, 300)),
+    ("o.o_date > 300", (301, 2 ** 31 - 1)),
+    ("o.o_date >= 300", (300, 2 ** 31 - 1)),
+    ("o.o_date BETWEEN 10 AND 20", (10, 20)),
+])
+def test_sql_comparisons_become_inclusive_ranges(cond, want):
+    p = sql.parse(f"SELECT COUNT(*) FROM fact f, orders o WHERE f.f_order = o.o_key AND {cond}", CATALOG)
+    assert [(c.rel, c.name, lo, hi) for c, lo, hi in p.ranges] == [("o", "o_date") + want]
+    assert [(a.rel, a.name, b.rel, b.name) for a, b in p.joins] == [("f", "f_order", "o", "o_key")]
+
+
+def test_sql_keywords_case_and_unqualified_columns():
+    """Keywords in any case, a trailing semicolon, AS aliases in the select
+    list and columns without an alias when only one table has them."""
+    text = ("select count(*) as n from fact f, orders o "
+            "where f_order = o_key and o_date between 5 and 9 group by o_cust;")
+    p = sql.parse(text, CATALOG)
+    assert p.select == [("count",)]
+    assert [(a.rel, a.name, b.rel, b.name) for a, b in p.joins] == [("f", "f_order", "o", "o_key")]
+    assert [(c.rel, c.name, lo, hi) for c, lo, hi in p.ranges] == [("o", "o_date", 5, 9)]
+    assert [(c.rel, c.name) for c in p.group_by] == [("o", "o_cust")]
+    tr = sql.translate(text, CATALOG)
+    assert tr.aggregate == ("count",)
+    # the grouped key is an output vertex, the joined key is aggregated away
+    assert len(tr.vertices) == 2 and len(tr.alpha) == 1
+
+
+@pytest.mark.parametrize("text,msg", [
+    ("SELECT COUNT(*) FROM fact f, orders o WHERE f.f_order <> o.o_key", "unsupported comparison"),
+    ("SELECT COUNT(*) FROM fact f, orders o WHERE f.f_order < o.o_key", "only equi-joins"),
+    ("SELECT COUNT(*) FROM nowhere n", "unknown table"),
+    ("SELECT COUNT(*) FROM fact f WHERE g.f_order = 3", "unknown alias"),
+    ("SELECT COUNT(*) FROM fact f GROUP BY f.f_order extra", "unexpected"),
+    ("SELECT COUNT(*), SUM(f.price) FROM fact f", "exactly one aggregate"),
+    ("SELECT COUNT(*) FROM fact f WHERE f.f_order = 3 $", "cannot read"),
+])
+def test_sql_more_refusals(text, msg):
+    with pytest.raises(sql.SQLError) as e:
+        sql.translate(text, CATALOG)
+    assert msg in str(e.value)
