@@ -281,7 +281,9 @@ typedef struct {
  * the sizes are within 32x of each other and a binary-search probe of the
  * smaller into the larger otherwise; uint cap bs tests bits; bs cap bs ANDs
  * 128-bit words.  Count-only (Section 2.4: the core operation of an
- * attribute). */
+ * attribute).  Merge tiles and the other kinds run in two kernels (at most
+ * two launches); the tile count is read back once, so the call
+ * synchronises the context stream there. */
 lh_status lh_intersect_count_batch(lh_ctx *ctx, uint32_t npairs, const lh_set *a,
                                    const lh_set *b, uint64_t *counts);
 
