@@ -491,7 +491,7 @@ lh_status lh_plan_exhaustive(lh_ctx *ctx, const lh_query *q, const lh_relation_d
     lh_candidate_orders(q, orders);
     // candidates in the order of the Section 4 cost estimate, so that fast
     // plans come early; each later run is cut once it takes 1.25x the best
-    // time seen so far (it cannot be the fastest), which keeps the judge
+    // time seen so far (it cannot be the fastest), which keeps the search
     // exhaustive while bounding the time spent on hopeless plans
     {
         uint64_t cards[LH_MAX_EDGES];
