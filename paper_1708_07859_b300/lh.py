@@ -244,10 +244,6 @@ def to_device_u32(a, device="cuda"):
     return torch.from_numpy(a.view(np.int32)).to(device)
 
 
-def u32_to_numpy(t):
-    return t.detach().cpu().numpy().view(np.uint32)
-
-
 # ----------------------------------------------------------------- objects
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
